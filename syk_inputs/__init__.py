@@ -1,0 +1,138 @@
+"""Seeded synthetic inputs for the sparse-SYK workloads.
+
+This module is shared by the CPU oracle, the tests and the benchmark.  It holds
+only input generation: coupling draws, random states and a counter-based
+generator.  It computes nothing that the method itself computes (no Majorana
+algebra, no Hamiltonian action, no time evolution).
+
+Workload recipe (the paper's ensemble, main text around Eq. (1)):
+  * every quadruple 0 <= i < j < k < l < N is kept independently with
+    probability p (a Bernoulli mask), with p = k_sp * N / C(N, 4) so that the
+    expected number of kept terms is k_sp * N (sparsity parameter k);
+  * each kept coupling J is Gaussian with mean 0 and variance 3! J0^2/(p N^3)
+    in the chi-normalisation ({chi_i, chi_j} = delta_ij);
+  * couplings for realisation r use numpy PCG64(1000 + r) unless a seed is
+    given;
+  * a typical (Haar-like) state is an i.i.d. complex Gaussian vector over the
+    full 2^(N/2) space, normalised over the full space; its two parity blocks
+    are returned separately and are *not* renormalised.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+__all__ = [
+    "all_quads",
+    "sample_sparse_syk",
+    "sample_dense_syk",
+    "random_state",
+    "philox4x32_10",
+    "philox_state",
+]
+
+
+def all_quads(N: int) -> np.ndarray:
+    """All index quadruples i<j<k<l<N in lexicographic order, int32 [C(N,4), 4]."""
+    if N < 4:
+        return np.zeros((0, 4), dtype=np.int32)
+    return np.array(list(itertools.combinations(range(N), 4)), dtype=np.int32)
+
+
+def sample_sparse_syk(N: int, k: float, seed: int | None = None, r: int = 0, J0: float = 1.0):
+    """Draw one sparse-SYK realisation.
+
+    Returns (quads int32 [T,4], J float64 [T], p).  T is random (Bernoulli mask).
+    """
+    rng = np.random.Generator(np.random.PCG64(1000 + r if seed is None else seed))
+    q = all_quads(N)
+    C = q.shape[0]
+    p = min(1.0, k * N / C)
+    keep = rng.random(C) < p
+    quads = q[keep]
+    var = 6.0 * J0 * J0 / (p * N ** 3)
+    J = rng.normal(0.0, math.sqrt(var), size=quads.shape[0])
+    return quads.astype(np.int32), J.astype(np.float64), p
+
+
+def sample_dense_syk(N: int, seed: int = 0, J0: float = 1.0):
+    """Dense SYK (p = 1): every quadruple, J ~ N(0, 3! J0^2 / N^3)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    quads = all_quads(N)
+    J = rng.normal(0.0, math.sqrt(6.0 * J0 * J0 / N ** 3), size=quads.shape[0])
+    return quads, J, 1.0
+
+
+def random_state(N: int, seed: int, dtype=np.complex128):
+    """Typical state over the full 2^(N/2) space: (psi_U, psi_D), each 2^(N/2-1).
+
+    Gaussian real and imaginary parts, normalised so that
+    ||psi_U||^2 + ||psi_D||^2 = 1.
+    """
+    D = 1 << (N // 2 - 1)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.normal(size=(2, D)) + 1j * rng.normal(size=(2, D))
+    v /= np.linalg.norm(v)
+    return v[0].astype(dtype), v[1].astype(dtype)
+
+
+# --- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+# easy as 1, 2, 3", SC'11).  Written from the published definition: a 4-word
+# counter and 2-word key; each round multiplies words 0 and 2 by two constants
+# (full 64-bit products split into hi/lo halves), XORs the high halves with the
+# other counter words and the key, and permutes; the key is bumped by two
+# Weyl constants between rounds.
+_PM0 = np.uint64(0xD2511F53)
+_PM1 = np.uint64(0xCD9E8D57)
+_PW0 = np.uint64(0x9E3779B9)
+_PW1 = np.uint64(0xBB67AE85)
+_M32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(ctr, key):
+    """Vectorised Philox4x32-10.  ctr: uint [...,4]; key: uint [...,2] -> uint32 [...,4]."""
+    c = [np.asarray(ctr[..., i], dtype=np.uint64) & _M32 for i in range(4)]
+    k0 = np.asarray(key[..., 0], dtype=np.uint64) & _M32
+    k1 = np.asarray(key[..., 1], dtype=np.uint64) & _M32
+    for rnd in range(10):
+        if rnd:
+            k0 = (k0 + _PW0) & _M32
+            k1 = (k1 + _PW1) & _M32
+        p0 = _PM0 * c[0]
+        p1 = _PM1 * c[2]
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _M32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _M32
+        c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]
+    return np.stack(c, axis=-1).astype(np.uint32)
+
+
+def philox_state(N: int, seed: int, state_id: int, idx=None):
+    """Counter-based typical state: unnormalised complex Gaussian amplitudes.
+
+    Amplitude number g in [0, 2D) (g = block * D + m, block 0 = U, 1 = D) uses
+    counter (g mod 2^32, g >> 32, state_id mod 2^32, state_id >> 32) and key
+    (seed mod 2^32, seed >> 32).  Output words w0..w3 give two 53-bit uniforms
+    u1 = ((w1:w0 >> 11) + 1) / 2^53 in (0, 1] and u2 = (w3:w2 >> 11) / 2^53 in
+    [0, 1); the amplitude is sqrt(-2 ln u1) * (cos 2 pi u2 + i sin 2 pi u2)
+    (Box-Muller).  Returns complex128 values for the requested global indices
+    (all 2D if idx is None).  Normalisation is left to the caller.
+    """
+    D = 1 << (N // 2 - 1)
+    g = np.arange(2 * D, dtype=np.uint64) if idx is None else np.asarray(idx, dtype=np.uint64)
+    ctr = np.zeros(g.shape + (4,), dtype=np.uint64)
+    ctr[..., 0] = g & _M32
+    ctr[..., 1] = g >> np.uint64(32)
+    ctr[..., 2] = np.uint64(state_id & 0xFFFFFFFF)
+    ctr[..., 3] = np.uint64(state_id >> 32)
+    key = np.zeros(g.shape + (2,), dtype=np.uint64)
+    key[..., 0] = np.uint64(seed & 0xFFFFFFFF)
+    key[..., 1] = np.uint64(seed >> 32)
+    w = philox4x32_10(ctr, key).astype(np.uint64)
+    a = ((w[..., 1] << np.uint64(32)) | w[..., 0]) >> np.uint64(11)
+    b = ((w[..., 3] << np.uint64(32)) | w[..., 2]) >> np.uint64(11)
+    u1 = (a.astype(np.float64) + 1.0) * 2.0 ** -53
+    u2 = b.astype(np.float64) * 2.0 ** -53
+    r = np.sqrt(-2.0 * np.log(u1))
+    return r * np.cos(2 * np.pi * u2) + 1j * r * np.sin(2 * np.pi * u2)
