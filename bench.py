@@ -1,0 +1,303 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse-SYK OTOC hot path: H psi at N = 64.
+
+Workload (the N = 64 configuration the headline metric is quoted on): one
+sparse-SYK realisation with N = 64 Majoranas, k = 4 (Bernoulli mask, ~256
+terms), Jordan-Wigner representation, one parity block of D = 2^31
+amplitudes (complex64: 16 GiB per vector).  A step is one H_UU psi through
+syk_apply_H with psi and Phi resident in HBM (both far larger than the
+126 MB L2, so no L2 flush is needed between steps).  The float64 variant
+(complex128, 32 GiB per vector) is reported alongside.
+
+Multi-GPU: replicas only (each rank its own realisation, no collective on the
+data path); value = all ranks' term*amplitude updates / max time over ranks.
+
+`--impl reference` times the CPU oracle (sampled rows of H psi from the
+definition) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import importlib.util
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·ψ Gterm·amp/s at N=64 (fp32 vs fp64); OTOC realizations/s; p50/p99 latency"
+UNIT = "Gterm·amp/s"
+ISSUE_SLOTS_PER_TERM_AMP = 3  # 2 FP32 FMA + 1 load per term x amplitude
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=64)
+    ap.add_argument("--k", type=float, default=4.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, T):
+    return {"workload": f"sparse SYK H·psi, N={args.N}, k={args.k:g}, one parity block",
+            "N": args.N, "k": args.k, "terms": T, "D": 1 << (args.N // 2 - 1), "rep": "jw",
+            "states": 1, "l2": "inputs larger than L2 (16 GiB per vector), no flush"}
+
+
+# ------------------------------------------------------------------ clocks --
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- the oracle --
+def oracle_rows_rate(N, k, seconds=12.0, seed=77):
+    """CPU oracle: sampled rows of H_UU psi from the definition (basis-state
+    maps, numpy).  Returns (Gterm*amp/s, rows, T, threads)."""
+    import numpy as np
+
+    import syk_inputs as si
+    from oracle import hamiltonian as ham
+
+    q, J, _ = si.sample_sparse_syk(N, k, r=0)
+    T = len(J)
+    D = 1 << (N // 2 - 1)
+    rng = np.random.default_rng(seed)
+
+    def run(nrows):
+        rows = rng.integers(0, D, nrows).astype(np.uint64)
+        needed = []
+        ham.rows_of_Hpsi(N, q, J, "jw", 0, rows, lambda b, m: needed.append(m.copy()) or np.zeros(len(m)))
+        idx = np.unique(np.concatenate(needed))
+        vals = si.philox_state(N, seed, 0, idx)  # inputs, generated outside the timed region
+        lookup = lambda b, m: vals[np.searchsorted(idx, m)]
+        t0 = time.perf_counter()
+        ham.rows_of_Hpsi(N, q, J, "jw", 0, rows, lookup)
+        return time.perf_counter() - t0
+
+    dt = run(256)
+    nrows = int(min(1 << 20, max(256, 256 * seconds / max(dt, 1e-3))))
+    dt = run(nrows)
+    return T * nrows / dt / 1e9, nrows, T, 1
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(max(1, args.warmup)):
+        oracle_rows_rate(args.N, args.k, seconds=2.0)
+    for _ in range(max(1, args.steps)):
+        v, nrows, T, cores = oracle_rows_rate(args.N, args.k, seconds=3.0)
+        vals.append(v)
+    value = statistics.median(vals)
+    sample = f"{nrows} random rows of H_UU psi per step (of D=2^{args.N // 2 - 1}), T={T} terms"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": (time.perf_counter() - t0) * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, T),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours ----
+def build_lib():
+    spec = importlib.util.spec_from_file_location("_syk_build", os.path.join(ROOT, "paper_2311_00639_b300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+
+
+def time_matvecs(h, psi, out, steps, warmup, torch):
+    for _ in range(warmup):
+        h.apply_H(psi, 0, out=out)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        h.apply_H(psi, 0, out=out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def ours(args):
+    import numpy as np
+    import torch
+
+    build_lib()
+    import paper_2311_00639_b300 as syk
+    import syk_inputs as si
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    barrier = (lambda: dist.barrier()) if dist else (lambda: None)
+
+    q, J, _ = si.sample_sparse_syk(args.N, args.k, r=rank)
+    h = syk.Terms(args.N, q, J, dtype="c64")
+    T, D = h.n_terms, h.D
+    psi, _ = h.random_state(seed=1234, state_id=rank, blocks=(0,))
+    out = h.empty()
+    props = torch.cuda.get_device_properties(local)
+
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    dt = time_matvecs(h, psi, out, args.steps, args.warmup, torch)
+    clk = clocks.stop()
+    barrier()
+    if dist:
+        tt = torch.tensor([dt], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = tt.item()
+    per_step = dt / args.steps
+    value = world * T * D * args.steps / dt / 1e9
+
+    # e2e through the public API: pinned host psi -> device, H psi, result -> host
+    e2e = None
+    if not args.no_e2e:
+        hpsi = torch.empty(D, dtype=torch.complex64, pin_memory=True)
+        hout = torch.empty(D, dtype=torch.complex64, pin_memory=True)
+        hpsi.copy_(psi)
+        ke = max(1, min(3, args.steps))
+        for it in range(ke + 1):
+            if it == 1:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            psi.copy_(hpsi, non_blocking=True)
+            h.apply_H(psi, 0, out=out)
+            hout.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+        de = (time.perf_counter() - t0) / ke
+        e2e = {"value": world * T * D / de / 1e9, "unit": UNIT, "h2d_bytes_per_step": D * 8,
+               "d2h_bytes_per_step": D * 8, "ms_per_step": de * 1e3}
+        del hpsi, hout
+
+    # float64 states (complex128)
+    fp64 = None
+    if not args.no_fp64:
+        del out
+        psi64 = None
+        h64 = syk.Terms(args.N, q, J, dtype="c128")
+        psi64, _ = h64.random_state(seed=1234, state_id=rank, blocks=(0,))
+        out64 = h64.empty()
+        k64 = max(1, min(3, args.steps))
+        d64 = time_matvecs(h64, psi64, out64, k64, min(args.warmup, 2), torch)
+        fp64 = {"value": world * T * D * k64 / d64 / 1e9, "unit": UNIT, "ms_per_step": d64 * 1e3 / k64,
+                "dtype": "c128 (f64)"}
+        del psi64, out64
+        h64.close()
+
+    # roofline of the matvec kernel
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    peak_slots = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # Tslot/s
+    achieved_slots = ISSUE_SLOTS_PER_TERM_AMP * T * D / per_step / 1e12
+    t_bytes = 2 * D * 8 / (hbm * 1e9)
+    t_alu = ISSUE_SLOTS_PER_TERM_AMP * T * D / (peak_slots * 1e12)
+    roof = {"bound": "alu" if t_alu >= t_bytes else "hbm", "achieved": achieved_slots, "peak": peak_slots,
+            "unit": "Tslot/s", "frac": achieved_slots / peak_slots, "traffic": None,
+            "peak_source": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz (measured max clock)",
+            "algorithmic_bytes": 2 * D * 8, "hbm_time_ms": t_bytes * 1e3, "alu_time_ms": t_alu * 1e3,
+            "hbm_gbs_achieved": 2 * D * 8 / per_step / 1e9, "hbm_peak_gbs": hbm}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, nrows, _, cores = oracle_rows_rate(args.N, args.k, seconds=12.0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{nrows} random rows of H_UU psi (N={args.N}, T={T}) from the definition"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 states)", "data": "synthetic",
+                "config": {**workload_config(args, T), "parallelism": f"replicas x{world}"},
+                "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "fp64": fp64, "clocks": clk, "gpu": props.name}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * libsyk — matrix-free sparse-SYK OTOC path on one B300 (sm_103a).
+ *
+ * Paper: Garcia-Garcia, Liu, Verbaarschot, "Sparsity independent Lyapunov
+ * exponent in the SYK model" (arXiv 2311.00639).  Citations below name the
+ * paper's equations, sections and algorithms.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions (every call)
+ *   * N Majoranas, N even, 4 <= N <= 64.  L = N/2 - 1 qubits per parity block,
+ *     D = 2^L amplitudes per block.  chi_n = gamma_n / sqrt(2),
+ *     {chi_m, chi_n} = delta_mn (main text, below Eq. (1)).
+ *   * Qubit s is bit s of a basis index; sigma_y = [[0,-i],[i,0]] (the form
+ *     Algorithm 1 implements with coeff = lambda i^{#sigma_y}).
+ *   * Representation SYK_REP_PAPER: supplement Eq. (S1), compact form; block
+ *     U = top qubit 0, D = top qubit 1; block index m = the other L bits.
+ *     gamma_{N-1} has UD = -i, DU = +i; gamma_{N-2} blocks = sigma_z on qubit L-1.
+ *   * Representation SYK_REP_JW: gamma_{2s} = Z_0..Z_{s-1} X_s,
+ *     gamma_{2s+1} = Z_0..Z_{s-1} Y_s on N/2 qubits; block U = even popcount
+ *     of the full index, D = odd; block index m drops the top qubit.  Every
+ *     four-Majorana term flips at most four bits of m (best locality).
+ *   * A state of one block is D complex numbers (SYK_C64: interleaved float
+ *     re,im; SYK_C128: interleaved double re,im), contiguous.  `nstates`
+ *     states are stored one after another ([nstates][D]).
+ *   * Vector pointers are DEVICE pointers owned by the caller (e.g. torch
+ *     tensors); the library never frees caller memory.  Pointers must be
+ *     16-byte aligned.  Every call with a cudaStream_t is asynchronous on that
+ *     stream unless stated otherwise.
+ *   * Return value: SYK_OK (0) or a negative status.  syk_last_error() gives
+ *     the message of the last failing call on the calling thread.  No C++
+ *     exception crosses this interface.
+ * ---------------------------------------------------------------------------
+ */
+#ifndef SYK_H
+#define SYK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* syk_stream_t; /* == cudaStream_t */
+
+enum {
+  SYK_OK = 0,
+  SYK_EINVAL = -1,   /* invalid argument */
+  SYK_ENOMEM = -2,   /* device or host allocation failed */
+  SYK_ENOCONV = -3,  /* Krylov substep control did not converge */
+  SYK_ETIMEOUT = -4, /* a bounded device wait expired */
+  SYK_ECUDA = -5     /* CUDA runtime error */
+};
+enum { SYK_C64 = 0, SYK_C128 = 1 };
+enum { SYK_REP_JW = 0, SYK_REP_PAPER = 1 };
+enum { SYK_BLOCK_U = 0, SYK_BLOCK_D = 1 };
+enum { SYK_OTOC_TYPICAL = 0, SYK_OTOC_EXACT_TRACE = 1 };
+
+typedef struct syk_terms syk_terms_t;
+
+/* Summary of a compiled Hamiltonian (host struct). */
+typedef struct {
+  int N, L, dtype, rep;
+  int64_t D;           /* amplitudes per block */
+  int64_t n_input;     /* quadruples given */
+  int64_t n_terms;     /* Pauli strings after merging duplicates */
+  int64_t n_real;      /* strings with a real coefficient (the rest are i * real) */
+  int64_t n_xgroups;   /* distinct flip masks */
+  double sum_abs_coef; /* sum_t |c_t|, a bound on ||H_block|| */
+} syk_terms_info;
+
+/*
+ * syk_build_terms — compile H = sum_t J_t chi_i chi_j chi_k chi_l (Eq. (1)).
+ *   quads : HOST int32 [T][4], each row strictly increasing, entries in [0, N).
+ *   J     : HOST double [T], chi-normalised couplings (any real values).
+ *   dtype : SYK_C64 or SYK_C128 — the state type every later call uses.
+ *   rep   : SYK_REP_JW or SYK_REP_PAPER.
+ * Each term becomes one Pauli string on the L-qubit block, Phi[m] +=
+ * c (-1)^{popc(z & m)} psi[m ^ x], by the operator product rule of the
+ * supplement Sec. I.A (XOR of flip masks, phase from the sign pattern);
+ * duplicates are merged (supplement Sec. I.A, operator addition).  Terms are
+ * grouped by flip mask.  The table is uploaded to the current device; the
+ * handle owns it.  T = 0 is allowed (H = 0).  Errors: SYK_EINVAL (bad N,
+ * unsorted or out-of-range quad, non-finite J), SYK_ENOMEM, SYK_ECUDA.
+ */
+int syk_build_terms(int N, int64_t T, const int32_t* quads, const double* J, int dtype, int rep,
+                    syk_terms_t** out);
+int syk_terms_destroy(syk_terms_t* h);
+int syk_terms_get_info(const syk_terms_t* h, syk_terms_info* info);
+/*
+ * Copy the compiled table to HOST arrays of length info.n_terms (any may be
+ * NULL): flip mask x, sign mask z, coefficient per block (coef_U, coef_D)
+ * and imag flag (1 if the coefficient is i * coef).  Matrix element:
+ * (H_P psi)[m] = sum_t coef_P[t] * (imag ? i : 1) * (-1)^{popc(z[t] & m)} * psi[m ^ x[t]].
+ */
+int syk_terms_export(const syk_terms_t* h, uint32_t* x, uint32_t* z, double* coef_U, double* coef_D,
+                     uint8_t* imag);
+
+/*
+ * Host-only compilation (no CUDA call; usable without a GPU).  Same rules as
+ * syk_build_terms.  Writes up to `capacity` strings into the HOST arrays and
+ * the true count into *n_terms (arrays may be NULL to query the count).
+ */
+int syk_compile_terms_host(int N, int64_t T, const int32_t* quads, const double* J, int rep, int64_t capacity,
+                           int64_t* n_terms, uint32_t* x, uint32_t* z, double* coef_U, double* coef_D,
+                           uint8_t* imag);
+/*
+ * Host-only: chi_n from block P as (chi psi)[m] = c_P (-1)^{popc(z & m)} psi[m ^ x]
+ * in the other block; c_P = re[P] + i im[P] (arrays of 2).
+ */
+int syk_compile_chi_host(int N, int rep, int n, uint32_t* x, uint32_t* z, double* re, double* im);
+
+/*
+ * syk_apply_H — out = H_PP psi for block P (Algorithm 1, supplement
+ * Sec. I.A; K1 of the hot path).  psi, out: [nstates][D] device, dtype of h;
+ * out must not overlap psi.  Errors: SYK_EINVAL (null pointer, bad block,
+ * overlap, nstates < 1), SYK_ECUDA.
+ */
+int syk_apply_H(const syk_terms_t* h, int block, const void* psi, void* out, int64_t nstates,
+                syk_stream_t stream);
+
+/*
+ * syk_apply_chi — out = chi_i psi, mapping block from_block to the other
+ * block (supplement, parity-block OTOC formula; for the paper representation
+ * chi_{N-1}: U->D times +i/sqrt2, D->U times -i/sqrt2, and chi_{N-2}: sigma_z on
+ * qubit L-1 over sqrt2).  For i with an empty flip mask (chi_{N-1}, chi_{N-2}
+ * in both representations) out may alias psi; otherwise it must not.
+ */
+int syk_apply_chi(const syk_terms_t* h, int i, int from_block, const void* psi, void* out,
+                  int64_t nstates, syk_stream_t stream);
+
+/*
+ * syk_random_state — typical-state amplitudes (supplement: Haar-random
+ * state; K4).  Writes UNNORMALISED i.i.d. standard complex Gaussians
+ * (E|a|^2 = 2) into psi_U and psi_D (D each).  Amplitude g = block*D + m uses
+ * Philox4x32-10 (Salmon et al., SC'11) with counter (g lo, g hi, state_id lo,
+ * state_id hi) and key (seed lo, seed hi); words w0..w3 give
+ * u1 = ((w1:w0 >> 11) + 1) 2^-53, u2 = (w3:w2 >> 11) 2^-53 and
+ * a = sqrt(-2 ln u1) (cos 2 pi u2 + i sin 2 pi u2).  Either pointer may be NULL.
+ */
+int syk_random_state(const syk_terms_t* h, uint64_t seed, uint64_t state_id, void* psi_U, void* psi_D,
+                     syk_stream_t stream);
+
+/* Krylov (Lanczos) propagation parameters.  Zero fields take the defaults. */
+typedef struct {
+  int m;            /* Krylov dimension per substep (default 30, max 64) */
+  double tol;       /* relative error target per evolve (default 1e-12 C128, 1e-6 C64) */
+  int max_substeps; /* default 1000 */
+  int reorth;       /* 1: full re-orthogonalisation (classical Gram-Schmidt twice) */
+  int two_pass;     /* 1: do not store the basis; regenerate it in a second pass */
+} syk_krylov_params;
+
+typedef struct {
+  int64_t matvecs;
+  int64_t substeps;
+  double err_est; /* sum of accepted local error estimates (relative) */
+} syk_krylov_stats;
+
+/* Bytes of device workspace syk_krylov_evolve needs for these parameters. */
+size_t syk_krylov_workspace_bytes(const syk_terms_t* h, const syk_krylov_params* p);
+
+/*
+ * syk_krylov_evolve — y = e^{-(tau + i t) H_PP} x for each of nstates states
+ * (supplement Sec. I.A: restarted Krylov method for the state time
+ * evolution; here Lanczos with an a-posteriori error estimate and substep
+ * control in the manner of Expokit, Sidje 1998).  Lanczos scalars (alpha,
+ * beta, norms, the tridiagonal eigensystem and exponential) are float64 on
+ * the device for both dtypes.  y may alias x.  workspace: device, at least
+ * syk_krylov_workspace_bytes().  stats: HOST, may be NULL.  The call returns
+ * after the result is complete on `stream` (it synchronises once per
+ * substep to read the accepted step).  Errors: SYK_EINVAL, SYK_ENOCONV,
+ * SYK_ECUDA.
+ */
+int syk_krylov_evolve(const syk_terms_t* h, int block, double tau, double t, const void* x, void* y,
+                      int64_t nstates, const syk_krylov_params* p, void* workspace, size_t ws_bytes,
+                      syk_krylov_stats* stats, syk_stream_t stream);
+
+/*
+ * syk_otoc — regularised OTOC, Eq. (2), via the parity-block single-state
+ * formula of the supplement:
+ *   F_P(t) = <psi_P| e^{(it-b/8)H_PP} chi_a e^{-(it+b/4)H_QQ} chi_b
+ *            e^{(it-b/4)H_PP} chi_a e^{-(it+b/4)H_QQ} chi_b e^{-bH_PP/8} |psi_P>,
+ *   F = F_U + F_D,  OTOC(t) = Re mean_s F_s(t) / Re mean_s F_s(0).
+ *   a, b      : Majorana indices (the paper: a = N-1, b = N-2).
+ *   t_grid    : HOST double [n_t], non-decreasing, t_grid[0] = 0.
+ *   mode      : SYK_OTOC_TYPICAL (states from psi_opt, else from
+ *               syk_random_state(seed, s) normalised over both blocks) or
+ *               SYK_OTOC_EXACT_TRACE (all 2D basis states; F = Tr[...]/2D).
+ *   psi_opt   : optional DEVICE [n_states][2][D] (U block then D block),
+ *               used as given (normalise them yourself).
+ *   F_raw     : HOST double [n_states][n_t][2] (re, im) per state (exact trace:
+ *               n_states is ignored and one row is written), may be NULL.
+ *   otoc      : HOST double [n_t], may be NULL.
+ * Allocates its own device workspace for the call and frees it before
+ * returning; blocks until the host outputs are written.
+ */
+int syk_otoc(const syk_terms_t* h, int a, int b, double beta, const double* t_grid, int n_t, int mode,
+             int n_states, uint64_t seed, const void* psi_opt, const syk_krylov_params* p, double* F_raw,
+             double* otoc, syk_krylov_stats* stats, syk_stream_t stream);
+
+/* Message of the last failing call on this thread (always NUL-terminated). */
+int syk_last_error(char* buf, size_t n);
+/* Library version string. */
+const char* syk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYK_H */

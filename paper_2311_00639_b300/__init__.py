@@ -1,0 +1,13 @@
+"""Sparse-SYK OTOC hot path on B300 (sm_103a): a thin binding of libsyk.
+
+The compute path is the CUDA library ``libsyk.so`` (sources in ``csrc/``,
+C-ABI in ``include/syk.h``); importing this package loads it and fails loudly
+if it has not been built (``python paper_2311_00639_b300/build.py``).  There
+is no CPU fallback.
+"""
+from ._lib import LIB_PATH, SykError, load
+from .api import KrylovStats, Terms, compile_chi_host, compile_terms_host
+
+load()
+
+__all__ = ["Terms", "KrylovStats", "SykError", "compile_terms_host", "compile_chi_host", "LIB_PATH", "load"]

@@ -1,0 +1,83 @@
+"""ctypes declarations of libsyk (include/syk.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsyk.so")
+
+SYK_OK, SYK_EINVAL, SYK_ENOMEM, SYK_ENOCONV, SYK_ETIMEOUT, SYK_ECUDA = 0, -1, -2, -3, -4, -5
+SYK_C64, SYK_C128 = 0, 1
+SYK_REP_JW, SYK_REP_PAPER = 0, 1
+SYK_OTOC_TYPICAL, SYK_OTOC_EXACT_TRACE = 0, 1
+
+
+class TermsInfo(C.Structure):
+    _fields_ = [("N", C.c_int), ("L", C.c_int), ("dtype", C.c_int), ("rep", C.c_int), ("D", C.c_int64),
+                ("n_input", C.c_int64), ("n_terms", C.c_int64), ("n_real", C.c_int64),
+                ("n_xgroups", C.c_int64), ("sum_abs_coef", C.c_double)]
+
+
+class KrylovParams(C.Structure):
+    _fields_ = [("m", C.c_int), ("tol", C.c_double), ("max_substeps", C.c_int), ("reorth", C.c_int),
+                ("two_pass", C.c_int)]
+
+
+class KrylovStats(C.Structure):
+    _fields_ = [("matvecs", C.c_int64), ("substeps", C.c_int64), ("err_est", C.c_double)]
+
+
+# name -> (restype, argtypes); every symbol include/syk.h declares.
+_P = C.c_void_p
+_I, _I64, _U64, _D, _SZ = C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_size_t
+SIGNATURES = {
+    "syk_build_terms": (_I, [_I, _I64, _P, _P, _I, _I, C.POINTER(_P)]),
+    "syk_terms_destroy": (_I, [_P]),
+    "syk_terms_get_info": (_I, [_P, C.POINTER(TermsInfo)]),
+    "syk_terms_export": (_I, [_P, _P, _P, _P, _P, _P]),
+    "syk_compile_terms_host": (_I, [_I, _I64, _P, _P, _I, _I64, C.POINTER(_I64), _P, _P, _P, _P, _P]),
+    "syk_compile_chi_host": (_I, [_I, _I, _I, _P, _P, _P, _P]),
+    "syk_apply_H": (_I, [_P, _I, _P, _P, _I64, _P]),
+    "syk_apply_chi": (_I, [_P, _I, _I, _P, _P, _I64, _P]),
+    "syk_random_state": (_I, [_P, _U64, _U64, _P, _P, _P]),
+    "syk_krylov_workspace_bytes": (_SZ, [_P, C.POINTER(KrylovParams)]),
+    "syk_krylov_evolve": (_I, [_P, _I, _D, _D, _P, _P, _I64, C.POINTER(KrylovParams), _P, _SZ,
+                               C.POINTER(KrylovStats), _P]),
+    "syk_otoc": (_I, [_P, _I, _I, _D, _P, _I, _I, _I, _U64, _P, C.POINTER(KrylovParams), _P, _P,
+                      C.POINTER(KrylovStats), _P]),
+    "syk_last_error": (_I, [C.c_char_p, _SZ]),
+    "syk_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load libsyk.so from the package directory; fail loudly if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libsyk.so not found at {LIB_PATH}; build it with `python paper_2311_00639_b300/build.py`")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SykError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def check(rc: int):
+    if rc != SYK_OK:
+        buf = C.create_string_buffer(1024)
+        load().syk_last_error(buf, 1024)
+        raise SykError(rc, buf.value.decode(errors="replace"))

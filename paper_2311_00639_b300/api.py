@@ -1,0 +1,208 @@
+"""Python binding of libsyk: torch tensors in, C-ABI calls out.
+
+Argument marshalling only — every step of the path runs in the CUDA library.
+Torch provides device memory and streams.  Names follow include/syk.h.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+_DT = {"c64": L.SYK_C64, "c128": L.SYK_C128}
+_REP = {"jw": L.SYK_REP_JW, "paper": L.SYK_REP_PAPER}
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _tdtype(dtype: str):
+    torch = _torch()
+    return torch.complex64 if dtype == "c64" else torch.complex128
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_arrays(quads, J):
+    q = np.ascontiguousarray(np.asarray(quads, dtype=np.int32).reshape(-1, 4))
+    j = np.ascontiguousarray(np.asarray(J, dtype=np.float64).reshape(-1))
+    if q.shape[0] != j.shape[0]:
+        raise ValueError("quads and J lengths differ")
+    return q, j
+
+
+def compile_terms_host(N: int, quads, J, rep: str = "jw") -> dict:
+    """Host-only term compilation (no GPU): x, z, coef_U, coef_D, imag arrays."""
+    lib = L.load()
+    q, j = _host_arrays(quads, J)
+    n = C.c_int64(0)
+    L.check(lib.syk_compile_terms_host(N, q.shape[0], q.ctypes.data, j.ctypes.data, _REP[rep], 0, C.byref(n),
+                                       None, None, None, None, None))
+    cnt = n.value
+    out = {"x": np.zeros(cnt, np.uint32), "z": np.zeros(cnt, np.uint32), "coef_U": np.zeros(cnt),
+           "coef_D": np.zeros(cnt), "imag": np.zeros(cnt, np.uint8)}
+    L.check(lib.syk_compile_terms_host(N, q.shape[0], q.ctypes.data, j.ctypes.data, _REP[rep], cnt, C.byref(n),
+                                       out["x"].ctypes.data, out["z"].ctypes.data, out["coef_U"].ctypes.data,
+                                       out["coef_D"].ctypes.data, out["imag"].ctypes.data))
+    return out
+
+
+def compile_chi_host(N: int, n: int, rep: str = "jw") -> dict:
+    lib = L.load()
+    x, z = C.c_uint32(0), C.c_uint32(0)
+    re, im = (C.c_double * 2)(), (C.c_double * 2)()
+    L.check(lib.syk_compile_chi_host(N, _REP[rep], n, C.byref(x), C.byref(z), re, im))
+    return {"x": x.value, "z": z.value, "coef": [complex(re[0], im[0]), complex(re[1], im[1])]}
+
+
+class KrylovStats:
+    def __init__(self, s: L.KrylovStats):
+        self.matvecs, self.substeps, self.err_est = s.matvecs, s.substeps, s.err_est
+
+    def __repr__(self):
+        return f"KrylovStats(matvecs={self.matvecs}, substeps={self.substeps}, err_est={self.err_est:.3g})"
+
+
+def _params(m=30, tol=None, max_substeps=0, reorth=False, two_pass=False):
+    return L.KrylovParams(int(m), float(tol or 0.0), int(max_substeps), int(bool(reorth)), int(bool(two_pass)))
+
+
+class Terms:
+    """A compiled sparse-SYK Hamiltonian resident on the current CUDA device."""
+
+    def __init__(self, N: int, quads, J, dtype: str = "c64", rep: str = "jw"):
+        self._lib = L.load()
+        q, j = _host_arrays(quads, J)
+        h = C.c_void_p()
+        L.check(self._lib.syk_build_terms(N, q.shape[0], q.ctypes.data, j.ctypes.data, _DT[dtype], _REP[rep],
+                                          C.byref(h)))
+        self._h = h
+        self.N, self.dtype, self.rep = N, dtype, rep
+        info = L.TermsInfo()
+        L.check(self._lib.syk_terms_get_info(h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in L.TermsInfo._fields_}
+        self.D = info.D
+        self.n_terms = info.n_terms
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.syk_terms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- helpers
+    def empty(self, nstates: int = 1):
+        torch = _torch()
+        shape = (self.D,) if nstates == 1 else (nstates, self.D)
+        return torch.empty(shape, dtype=_tdtype(self.dtype), device="cuda")
+
+    def _check_vec(self, t, nstates=None):
+        torch = _torch()
+        if not t.is_cuda or t.dtype != _tdtype(self.dtype) or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA tensor of {_tdtype(self.dtype)}")
+        if t.numel() % self.D:
+            raise ValueError("tensor size is not a multiple of D")
+        return t.numel() // self.D
+
+    def export(self) -> dict:
+        n = self.n_terms
+        out = {"x": np.zeros(n, np.uint32), "z": np.zeros(n, np.uint32), "coef_U": np.zeros(n),
+               "coef_D": np.zeros(n), "imag": np.zeros(n, np.uint8)}
+        L.check(self._lib.syk_terms_export(self._h, out["x"].ctypes.data, out["z"].ctypes.data,
+                                           out["coef_U"].ctypes.data, out["coef_D"].ctypes.data,
+                                           out["imag"].ctypes.data))
+        return out
+
+    # -- hot path
+    def apply_H(self, psi, block: int, out=None, stream=None):
+        ns = self._check_vec(psi)
+        out = _torch().empty_like(psi) if out is None else out
+        self._check_vec(out)
+        L.check(self._lib.syk_apply_H(self._h, block, _ptr(psi), _ptr(out), ns, _stream(stream)))
+        return out
+
+    def apply_chi(self, i: int, psi, from_block: int, out=None, stream=None):
+        ns = self._check_vec(psi)
+        out = _torch().empty_like(psi) if out is None else out
+        self._check_vec(out)
+        L.check(self._lib.syk_apply_chi(self._h, i, from_block, _ptr(psi), _ptr(out), ns, _stream(stream)))
+        return out
+
+    def random_state(self, seed: int, state_id: int, stream=None, blocks=(0, 1)):
+        """Unnormalised Philox/Box-Muller amplitudes (psi_U, psi_D); a block
+        not listed in `blocks` is returned as None and not generated."""
+        u = self.empty() if 0 in blocks else None
+        d = self.empty() if 1 in blocks else None
+        L.check(self._lib.syk_random_state(self._h, C.c_uint64(seed), C.c_uint64(state_id),
+                                           None if u is None else _ptr(u), None if d is None else _ptr(d),
+                                           _stream(stream)))
+        return u, d
+
+    def workspace_bytes(self, **kp) -> int:
+        p = _params(**kp)
+        return int(self._lib.syk_krylov_workspace_bytes(self._h, C.byref(p)))
+
+    def krylov_evolve(self, x, block: int, tau: float, t: float, y=None, workspace=None, stream=None, **kp):
+        """y = exp(-(tau + i t) H_block) x.  Returns (y, KrylovStats)."""
+        torch = _torch()
+        ns = self._check_vec(x)
+        y = torch.empty_like(x) if y is None else y
+        self._check_vec(y)
+        p = _params(**kp)
+        nb = int(self._lib.syk_krylov_workspace_bytes(self._h, C.byref(p)))
+        if nb == 0:
+            L.check(L.SYK_EINVAL)
+        if workspace is None:
+            workspace = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        st = L.KrylovStats()
+        L.check(self._lib.syk_krylov_evolve(self._h, block, float(tau), float(t), _ptr(x), _ptr(y), ns,
+                                            C.byref(p), _ptr(workspace), workspace.numel(), C.byref(st),
+                                            _stream(stream)))
+        return y, KrylovStats(st)
+
+    def otoc(self, a: int, b: int, beta: float, t_grid, mode: str = "typical", n_states: int = 1, seed: int = 0,
+             psi=None, stream=None, **kp):
+        """Regularised OTOC.  Returns (F_raw complex [rows, n_t], otoc [n_t], KrylovStats).
+
+        psi: optional CUDA tensor [n_states, 2, D] (U then D block per state).
+        """
+        tg = np.ascontiguousarray(np.asarray(t_grid, dtype=np.float64))
+        md = L.SYK_OTOC_EXACT_TRACE if mode == "exact" else L.SYK_OTOC_TYPICAL
+        if psi is not None:
+            self._check_vec(psi)
+            n_states = psi.numel() // (2 * self.D)
+        rows = 1 if md == L.SYK_OTOC_EXACT_TRACE else n_states
+        F = np.zeros((rows, len(tg), 2))
+        o = np.zeros(len(tg))
+        p = _params(**kp)
+        st = L.KrylovStats()
+        L.check(self._lib.syk_otoc(self._h, a, b, float(beta), tg.ctypes.data, len(tg), md, int(n_states),
+                                   C.c_uint64(seed), None if psi is None else _ptr(psi), C.byref(p),
+                                   F.ctypes.data, o.ctypes.data, C.byref(st), _stream(stream)))
+        return F[..., 0] + 1j * F[..., 1], o, KrylovStats(st)

@@ -1,0 +1,84 @@
+// Internal declarations shared by the libsyk translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "syk.h"
+
+namespace syk {
+
+constexpr int kMaxKrylov = 64;   // largest Krylov dimension per substep
+constexpr int kMaxPartials = 2048;  // per-state reduction partials (>= any grid.x)
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define SYK_CUDA(expr)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      throw ::syk::Error(SYK_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+#define SYK_REQUIRE(cond, msg)                                   \
+  do {                                                           \
+    if (!(cond)) throw ::syk::Error(SYK_EINVAL, (msg));          \
+  } while (0)
+
+// One Pauli string acting inside a parity block (block-compressed form):
+//   (O psi)[m] = coef[P] * (imag ? i : 1) * (-1)^{popc(z & m)} * psi[m ^ x].
+struct BlockString {
+  uint32_t x = 0, z = 0;
+  double coef[2] = {0.0, 0.0};  // block U, block D
+  bool imag = false;
+};
+
+// A single Majorana restricted to block P -> 1-P, same output-index form,
+// with a complex coefficient per source block (chi = gamma / sqrt 2 included).
+struct ChiString {
+  uint32_t x = 0, z = 0;
+  double re[2] = {0, 0}, im[2] = {0, 0};
+};
+
+// Term compiler (terms.cpp).
+void compile_terms(int N, int rep, int64_t T, const int32_t* quads, const double* J,
+                   std::vector<BlockString>& out, int64_t& n_real, int64_t& n_xgroups);
+ChiString compile_chi(int N, int rep, int n);
+
+// Device view of a compiled term table, in compute precision Real.
+template <typename Real>
+struct TermsView {
+  const uint32_t* x;
+  const uint32_t* z;
+  const Real* coef;  // coefficients of the block being applied
+  int n_real;        // terms [0, n_real) real, [n_real, n) imaginary
+  int n;
+};
+
+}  // namespace syk
+
+struct syk_terms {
+  int N = 0, L = 0, dtype = 0, rep = 0, device = 0;
+  int64_t D = 0, n_input = 0, n_real = 0, n_xgroups = 0;
+  double sum_abs = 0.0;
+  std::vector<syk::BlockString> terms;
+  syk::ChiString chi[64];
+  // Device table: x[n], z[n], coef[2][n] in the dtype's precision.
+  void* d_mem = nullptr;
+  uint32_t* d_x = nullptr;
+  uint32_t* d_z = nullptr;
+  void* d_coef[2] = {nullptr, nullptr};
+  int n_sm = 148;
+  syk_terms() = default;
+  syk_terms(const syk_terms&) = delete;
+  syk_terms& operator=(const syk_terms&) = delete;
+  ~syk_terms() {
+    if (d_mem) cudaFree(d_mem);
+  }
+};

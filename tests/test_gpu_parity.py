@@ -1,0 +1,310 @@
+"""GPU parity: every hot-path call through the C-ABI against the CPU oracle.
+
+Tolerances (relative to the largest entry of the reference):
+  complex128 states: 1e-12 for H psi and chi psi, 1e-10 for Krylov results
+  (tol 1e-13 per evolve) and OTOC values; complex64 states: 1e-5 for H psi,
+  5e-5 for Krylov evolves, 1e-4 absolute on F(t) (|F| <= 1/4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import syk_inputs as si
+from oracle import dynamics as dyn
+from oracle import hamiltonian as ham
+from oracle import majorana as mj
+from oracle import otoc as ot
+
+pytestmark = pytest.mark.gpu
+
+TOL_H = {"c128": 1e-12, "c64": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def syk():
+    import paper_2311_00639_b300 as p
+
+    return p
+
+
+def torch():
+    import torch as t
+
+    return t
+
+
+def to_dev(a, dtype):
+    t = torch()
+    return t.from_numpy(np.ascontiguousarray(a)).to(device="cuda",
+                                                     dtype=t.complex64 if dtype == "c64" else t.complex128)
+
+
+def rel_err(got, ref):
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    return np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300)
+
+
+def rand_vec(D, seed, n=None):
+    rng = np.random.default_rng(seed)
+    shape = (D,) if n is None else (n, D)
+    return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+# ---------------------------------------------------------------- H psi ----
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("rep", ["jw", "paper"])
+@pytest.mark.parametrize("N", [4, 8, 10, 12, 14, 16, 18])
+def test_apply_H_vs_dense(syk, dtype, rep, N):
+    """Brute force: dense oracle blocks; sizes cover the one-warp path
+    (D < 32), the single-row path (32 <= D < 2048) and the tiled path."""
+    q, J, _ = si.sample_sparse_syk(N, 4, r=N)
+    if N == 4:
+        q, J = si.all_quads(4), np.array([0.7])
+    HU, HD = ham.blocks(ham.dense_H(N, q, J, rep), N, rep)
+    D = HU.shape[0]
+    psi = rand_vec(D, 1, n=3)
+    with syk.Terms(N, q, J, dtype=dtype, rep=rep) as h:
+        for blk, Hb in ((0, HU), (1, HD)):
+            out = h.apply_H(to_dev(psi, dtype), blk).cpu().numpy()
+            assert rel_err(out, psi @ Hb.T) < TOL_H[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_apply_H_N32_vs_csr(syk, dtype):
+    """N=32 (D = 32768, many tiles): oracle CSR matrix built from basis maps."""
+    N = 32
+    q, J, _ = si.sample_sparse_syk(N, 4, r=1)
+    psi = rand_vec(1 << 15, 2)
+    with syk.Terms(N, q, J, dtype=dtype) as h:
+        for blk in (0, 1):
+            ref = ham.csr_block(N, q, J, "jw", blk) @ psi
+            got = h.apply_H(to_dev(psi, dtype), blk).cpu().numpy()
+            assert rel_err(got, ref) < TOL_H[dtype]
+
+
+def test_apply_H_dense_syk_and_empty(syk):
+    """Dense SYK (every quadruple, many terms share a flip mask) and H = 0."""
+    N = 12
+    q, J, _ = si.sample_dense_syk(N, seed=3)
+    HU, _ = ham.blocks(ham.dense_H(N, q, J, "jw"), N, "jw")
+    psi = rand_vec(HU.shape[0], 4)
+    with syk.Terms(N, q, J, dtype="c128") as h:
+        assert rel_err(h.apply_H(to_dev(psi, "c128"), 0).cpu().numpy(), HU @ psi) < 1e-12
+    with syk.Terms(N, np.zeros((0, 4), np.int32), np.zeros(0), dtype="c128") as h:
+        assert h.n_terms == 0
+        assert np.all(h.apply_H(to_dev(psi, "c128"), 0).cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("N", [40, 64])
+def test_apply_H_sampled_rows_large(syk, dtype, N):
+    """N=40 and N=64 (the benchmark workload, same launch configuration):
+    sampled rows from the definition against a counter-based typical state."""
+    t = torch()
+    q, J, _ = si.sample_sparse_syk(N, 4, r=0)
+    rng = np.random.default_rng(5)
+    with syk.Terms(N, q, J, dtype=dtype) as h:
+        D = h.D
+        psiU, psiD = h.random_state(seed=77, state_id=3)
+        for blk, psi in ((0, psiU), (1, psiD)):
+            out = h.apply_H(psi, blk)
+            rows = np.concatenate([rng.integers(0, D, 2000), [0, D - 1]]).astype(np.uint64)
+            got = out[t.from_numpy(rows.astype(np.int64)).cuda()].cpu().numpy()
+            del out
+            at = lambda b, m: si.philox_state(N, 77, 3, np.uint64(b * D) + m)
+            ref = ham.rows_of_Hpsi(N, q, J, "jw", blk, rows, at)
+            assert rel_err(got, ref) < (2e-5 if dtype == "c64" else 1e-12)
+        del psiU, psiD
+        t.cuda.empty_cache()
+
+
+# ------------------------------------------------------------ random state --
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_random_state_matches_counter_definition(syk, dtype):
+    N = 20
+    q, J, _ = si.sample_sparse_syk(N, 4, r=0)
+    with syk.Terms(N, q, J, dtype=dtype) as h:
+        u, d = h.random_state(seed=2**40 + 5, state_id=2**33 + 9)
+        got = np.concatenate([u.cpu().numpy(), d.cpu().numpy()])
+    ref = si.philox_state(N, 2**40 + 5, 2**33 + 9)
+    assert rel_err(got, ref) < (1e-14 if dtype == "c128" else 1e-6)
+    # |a|^2 is exponential with mean 2 and standard deviation 2: allow 5 sigma
+    assert abs(np.mean(np.abs(ref) ** 2) - 2.0) < 5 * 2.0 / math.sqrt(ref.size)
+
+
+# -------------------------------------------------------------------- chi --
+@pytest.mark.parametrize("rep", ["jw", "paper"])
+@pytest.mark.parametrize("N", [8, 12, 16])
+def test_apply_chi_vs_dense(syk, rep, N):
+    X = mj.chis(N, rep)
+    q, J, _ = si.sample_sparse_syk(N, 4, r=2)
+    D = 1 << (N // 2 - 1)
+    psi = rand_vec(D, 7)
+    with syk.Terms(N, q, J, dtype="c128", rep=rep) as h:
+        for n in range(N):
+            for P in (0, 1):
+                ref = ham.block_of(X[n], N, rep, 1 - P, P) @ psi
+                got = h.apply_chi(n, to_dev(psi, "c128"), P).cpu().numpy()
+                assert rel_err(got, ref) < 1e-14
+
+
+def test_chi_anticommutators_on_vectors_N32(syk):
+    """{chi_i, chi_j} psi = delta_ij psi for vectors of the N=32 blocks."""
+    t = torch()
+    N = 32
+    q, J, _ = si.sample_sparse_syk(N, 4, r=3)
+    psi = to_dev(rand_vec(1 << 15, 8), "c128")
+    with syk.Terms(N, q, J, dtype="c128") as h:
+        pairs = [(0, 0), (0, 1), (5, 17), (31, 30), (N - 1, N - 2), (N - 1, N - 1), (13, 28), (29, 3)]
+        for i, j in pairs:
+            for P in (0, 1):
+                a = h.apply_chi(i, h.apply_chi(j, psi, P), 1 - P)
+                b = h.apply_chi(j, h.apply_chi(i, psi, P), 1 - P)
+                ref = psi * (1.0 if i == j else 0.0)
+                assert t.max(t.abs(a + b - ref)).item() < 1e-14
+
+
+# --------------------------------------------------------------- Krylov ----
+ZS = [(0.0, 0.7), (0.0, -4.0), (1.25, 0.0), (2.5, 3.0), (0.625, -7.5)]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("two_pass", [False, True])
+def test_krylov_vs_exact_N16(syk, dtype, two_pass):
+    N = 16
+    q, J, _ = si.sample_sparse_syk(N, 4, r=4)
+    HU, HD = ham.blocks(ham.dense_H(N, q, J, "jw"), N, "jw")
+    eig = (dyn.eig(HU), dyn.eig(HD))
+    x = rand_vec(HU.shape[0], 9)
+    tol = 1e-13 if dtype == "c128" else 1e-6
+    lim = 1e-10 if dtype == "c128" else 5e-5
+    with syk.Terms(N, q, J, dtype=dtype) as h:
+        for tau, tt in ZS:
+            for blk, Hb in ((0, HU), (1, HD)):
+                y, st = h.krylov_evolve(to_dev(x, dtype), blk, tau, tt, m=30, tol=tol, two_pass=two_pass)
+                ref = dyn.evolve(Hb, complex(tau, tt), x, eig[blk])
+                assert rel_err(y.cpu().numpy(), ref) < lim, (tau, tt, blk, st)
+
+
+def test_krylov_single_term_closed_form(syk):
+    """H = J chi chi chi chi: e^{-zH} = cosh(zJ/4) - sinh(zJ/4) H/(J/4), also
+    exercising the lucky-breakdown path (the Krylov space has dimension 2)."""
+    N = 20
+    q = np.array([[2, 7, 11, 19]], dtype=np.int32)
+    Jv = np.array([0.9])
+    x = rand_vec(1 << 9, 10)
+    with syk.Terms(N, q, Jv, dtype="c128") as h:
+        Hx = h.apply_H(to_dev(x, "c128"), 0).cpu().numpy()
+        w = Jv[0] / 4
+        for z in (0.5, 3.0 + 2.0j, -6.0j):
+            y, st = h.krylov_evolve(to_dev(x, "c128"), 0, z.real, z.imag)
+            ref = np.cosh(z * w) * x - np.sinh(z * w) * Hx / w
+            assert rel_err(y.cpu().numpy(), ref) < 1e-12
+            assert st.substeps == 1
+
+
+def test_krylov_N24_vs_expm_multiply_and_invariants(syk):
+    t = torch()
+    N = 24
+    q, J, _ = si.sample_sparse_syk(N, 4, r=5)
+    Hc = ham.csr_block(N, q, J, "jw", 1)
+    x = rand_vec(1 << 11, 11)
+    with syk.Terms(N, q, J, dtype="c128") as h:
+        for z, reorth in ((3.0j, False), (1.5 + 2.0j, True), (4.0 - 12.0j, False)):
+            y, _ = h.krylov_evolve(to_dev(x, "c128"), 1, z.real, z.imag, tol=1e-13, reorth=reorth)
+            assert rel_err(y.cpu().numpy(), dyn.evolve_sparse(Hc, z, x)) < 1e-10
+        # unitarity and e^{+iHt} e^{-iHt} = 1 at N = 32 (no oracle needed)
+    N = 32
+    q, J, _ = si.sample_sparse_syk(N, 4, r=6)
+    x = to_dev(rand_vec(1 << 15, 12), "c128")
+    with syk.Terms(N, q, J, dtype="c128") as h:
+        y, _ = h.krylov_evolve(x, 0, 0.0, 5.0)
+        assert abs(t.linalg.vector_norm(y).item() / t.linalg.vector_norm(x).item() - 1) < 1e-12
+        back, _ = h.krylov_evolve(y, 0, 0.0, -5.0)
+        assert t.max(t.abs(back - x)).item() / t.max(t.abs(x)).item() < 1e-11
+        # semigroup: e^{-z1 H} e^{-z2 H} = e^{-(z1+z2) H}
+        a, _ = h.krylov_evolve(x, 0, 0.5, 1.0)
+        a, _ = h.krylov_evolve(a, 0, 0.25, 2.0)
+        b, _ = h.krylov_evolve(x, 0, 0.75, 3.0)
+        assert t.max(t.abs(a - b)).item() / t.max(t.abs(b)).item() < 1e-11
+        # in-place (y aliases x) and batched states
+        xs = to_dev(rand_vec(1 << 15, 13, n=2), "c128")
+        ref0, _ = h.krylov_evolve(xs[0].clone(), 0, 0.3, 0.4)
+        h.krylov_evolve(xs, 0, 0.3, 0.4, y=xs)
+        assert t.max(t.abs(xs[0] - ref0)).item() < 1e-13
+
+
+def test_krylov_zero_vector_and_zero_time(syk):
+    t = torch()
+    N = 16
+    q, J, _ = si.sample_sparse_syk(N, 4, r=7)
+    with syk.Terms(N, q, J, dtype="c128") as h:
+        z = t.zeros(h.D, dtype=t.complex128, device="cuda")
+        y, _ = h.krylov_evolve(z, 0, 1.0, 2.0)
+        assert t.count_nonzero(y).item() == 0
+        x = to_dev(rand_vec(h.D, 1), "c128")
+        y, st = h.krylov_evolve(x, 0, 0.0, 0.0)
+        assert t.equal(y, x) and st.matvecs == 0
+
+
+# ----------------------------------------------------------------- OTOC ----
+@pytest.mark.parametrize("rep", ["jw", "paper"])
+@pytest.mark.parametrize("beta", [0.0, 5.0])
+def test_otoc_same_state_vs_oracle_N12(syk, rep, beta):
+    N = 12
+    q, J, _ = si.sample_sparse_syk(N, 4, r=8)
+    H = ham.dense_H(N, q, J, rep)
+    HU, HD = ham.blocks(H, N, rep)
+    X = mj.chis(N, rep)
+    ts = np.array([0.0, 0.5, 1.0, 2.5, 4.0])
+    states = [si.random_state(N, seed=40 + s) for s in range(2)]
+    psi = np.stack([np.stack(s) for s in states])  # [S, 2, D]
+    with syk.Terms(N, q, J, dtype="c128", rep=rep) as h:
+        for a, b in ((N - 1, N - 2), (3, 7)):
+            F, o, st = h.otoc(a, b, beta, ts, psi=to_dev(psi, "c128"), tol=1e-13)
+            for s in range(2):
+                ref = ot.F_state_blocks(N, rep, HU, HD, X, a, b, beta, ts, *states[s])
+                assert np.max(np.abs(F[s] - ref)) < 1e-10
+            mean = np.mean([ot.F_state_blocks(N, rep, HU, HD, X, a, b, beta, ts, *s) for s in states], axis=0)
+            assert np.max(np.abs(o - ot.normalise(mean))) < 1e-9
+
+
+def test_otoc_beta0_t0_is_minus_quarter_typical(syk):
+    N = 20
+    q, J, _ = si.sample_sparse_syk(N, 4, r=9)
+    with syk.Terms(N, q, J, dtype="c128") as h:
+        F, o, _ = h.otoc(N - 1, N - 2, 0.0, [0.0], n_states=3, seed=123)
+        assert np.max(np.abs(F[:, 0] + 0.25)) < 1e-13
+        assert o[0] == 1.0
+
+
+@pytest.mark.parametrize("rep", ["jw", "paper"])
+def test_otoc_exact_trace_vs_oracle_N10(syk, rep):
+    N = 10
+    q, J, _ = si.sample_sparse_syk(N, 4, r=10)
+    H = ham.dense_H(N, q, J, rep)
+    X = mj.chis(N, rep)
+    ts = np.array([0.0, 1.0, 3.0])
+    with syk.Terms(N, q, J, dtype="c128", rep=rep) as h:
+        for beta in (0.0, 4.0):
+            F, o, _ = h.otoc(N - 1, N - 2, beta, ts, mode="exact", tol=1e-13)
+            ref = ot.F_trace(H, X, N - 1, N - 2, beta, ts)
+            assert np.max(np.abs(F[0] - ref)) < 1e-11
+            assert np.max(np.abs(o - ot.normalise(ref))) < 1e-10
+
+
+def test_otoc_c64_vs_oracle_N16(syk):
+    """complex64 states with float64 Lanczos scalars against the float64 oracle."""
+    N = 16
+    q, J, _ = si.sample_sparse_syk(N, 4, r=11)
+    HU, HD = ham.blocks(ham.dense_H(N, q, J, "jw"), N, "jw")
+    X = mj.chis(N, "jw")
+    ts = np.array([0.0, 1.0, 2.0, 5.0])
+    st = si.random_state(N, seed=3)
+    psi = np.stack([np.stack(st)])
+    with syk.Terms(N, q, J, dtype="c64") as h:
+        F, o, _ = h.otoc(N - 1, N - 2, 5.0, ts, psi=to_dev(psi, "c64"))
+    ref = ot.F_state_blocks(N, "jw", HU, HD, X, N - 1, N - 2, 5.0, ts, *st)
+    assert np.max(np.abs(F[0] - ref)) < 1e-4 * max(1.0, np.max(np.abs(ref)) * 4)
