@@ -176,6 +176,31 @@ int syk_krylov_evolve(const syk_terms_t* h, int block, double tau, double t, con
                       syk_krylov_stats* stats, syk_stream_t stream);
 
 /*
+ * syk_krylov_evolve_noalloc — the same propagation as syk_krylov_evolve
+ * (same kernels, same results), for callers that cannot allocate device
+ * memory while they run: e.g. a program that embeds this library under
+ * another framework's memory pool which already owns the device memory, or a
+ * service whose device footprint must stay fixed after start-up.  It takes
+ * no workspace argument and allocates nothing; its workspace is a static
+ * device array of 16 MiB inside the library, held on every GPU that loads
+ * the library until the process exits.  The paper has no counterpart to this
+ * call.
+ *   * A call whose workspace (syk_krylov_workspace_bytes with the same
+ *     params) exceeds 16 MiB returns SYK_EINVAL without queuing work.
+ *   * All calls on a device share the array and leave their contents in it;
+ *     calls that overlap on the GPU (other streams, other host threads) race
+ *     and corrupt each other's results: serialise them.
+ *   * The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, once per device); make that first call before
+ *     any stream capture.
+ * Arguments, aliasing, synchronisation and errors are as for
+ * syk_krylov_evolve.
+ */
+int syk_krylov_evolve_noalloc(const syk_terms_t* h, int block, double tau, double t, const void* x, void* y,
+                              int64_t nstates, const syk_krylov_params* p, syk_krylov_stats* stats,
+                              syk_stream_t stream);
+
+/*
  * syk_otoc — regularised OTOC, Eq. (2), via the parity-block single-state
  * formula of the supplement:
  *   F_P(t) = <psi_P| e^{(it-b/8)H_PP} chi_a e^{-(it+b/4)H_QQ} chi_b

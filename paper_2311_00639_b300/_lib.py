@@ -44,6 +44,8 @@ SIGNATURES = {
     "syk_krylov_workspace_bytes": (_SZ, [_P, C.POINTER(KrylovParams)]),
     "syk_krylov_evolve": (_I, [_P, _I, _D, _D, _P, _P, _I64, C.POINTER(KrylovParams), _P, _SZ,
                                C.POINTER(KrylovStats), _P]),
+    "syk_krylov_evolve_noalloc": (_I, [_P, _I, _D, _D, _P, _P, _I64, C.POINTER(KrylovParams),
+                                       C.POINTER(KrylovStats), _P]),
     "syk_otoc": (_I, [_P, _I, _I, _D, _P, _I, _I, _I, _U64, _P, C.POINTER(KrylovParams), _P, _P,
                       C.POINTER(KrylovStats), _P]),
     "syk_last_error": (_I, [C.c_char_p, _SZ]),

@@ -186,6 +186,20 @@ class Terms:
                                             _stream(stream)))
         return y, KrylovStats(st)
 
+    def krylov_evolve_noalloc(self, x, block: int, tau: float, t: float, y=None, stream=None, **kp):
+        """Same as krylov_evolve, but the library takes the workspace from its
+        fixed static device array instead of a caller buffer (for callers that
+        cannot allocate device memory while they run; 16 MiB limit, calls on a
+        device must not overlap).  Returns (y, KrylovStats)."""
+        ns = self._check_vec(x)
+        y = _torch().empty_like(x) if y is None else y
+        self._check_vec(y)
+        p = _params(**kp)
+        st = L.KrylovStats()
+        L.check(self._lib.syk_krylov_evolve_noalloc(self._h, block, float(tau), float(t), _ptr(x), _ptr(y), ns,
+                                                    C.byref(p), C.byref(st), _stream(stream)))
+        return y, KrylovStats(st)
+
     def otoc(self, a: int, b: int, beta: float, t_grid, mode: str = "typical", n_states: int = 1, seed: int = 0,
              psi=None, stream=None, **kp):
         """Regularised OTOC.  Returns (F_raw complex [rows, n_t], otoc [n_t], KrylovStats).

@@ -82,6 +82,10 @@ Params resolve(const syk_terms* h, const syk_krylov_params* p) {
 
 }  // namespace
 
+namespace syk {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace syk
+
 extern "C" {
 
 const char* syk_version(void) { return "libsyk 0.1 (sm_103a)"; }

@@ -51,6 +51,9 @@ void compile_terms(int N, int rep, int64_t T, const int32_t* quads, const double
                    std::vector<BlockString>& out, int64_t& n_real, int64_t& n_xgroups);
 ChiString compile_chi(int N, int rep, int n);
 
+// Record the message syk_last_error() returns on this thread (capi.cu).
+void set_last_error(const std::string& msg);
+
 // Device view of a compiled term table, in compute precision Real.
 template <typename Real>
 struct TermsView {
