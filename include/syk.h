@@ -67,6 +67,9 @@ typedef struct {
   int64_t n_real;      /* strings with a real coefficient (the rest are i * real) */
   int64_t n_xgroups;   /* distinct flip masks */
   double sum_abs_coef; /* sum_t |c_t|, a bound on ||H_block|| */
+  int64_t n_passes;    /* matvec passes (term groups with an L2-resident working set) */
+  int64_t device_error; /* 1 if a kernel on this handle hit its bounded-wait limit (then results
+                           are invalid); reading it synchronises with the device */
 } syk_terms_info;
 
 /*
@@ -87,6 +90,19 @@ int syk_build_terms(int N, int64_t T, const int32_t* quads, const double* J, int
                     syk_terms_t** out);
 int syk_terms_destroy(syk_terms_t* h);
 int syk_terms_get_info(const syk_terms_t* h, syk_terms_info* info);
+/*
+ * syk_terms_replan — regroup the terms into matvec passes.  Each pass fixes a
+ * set of high index bits that its terms do not flip and visits the block one
+ * fixed value of those bits at a time ("super-tile"), so that its inputs are
+ * re-read from L2; l2_budget_bytes bounds the super-tile size (default 2 MiB,
+ * used by syk_build_terms).  straggler_ratio > 0 (default 1.5, the best of a
+ * sweep on B300 at N = 64) lets the planner dissolve light passes, moving their
+ * terms into heavier passes that fetch them from HBM instead; 0 disables it.
+ * Synchronises the device and re-uploads the table; results are unchanged up
+ * to floating-point summation order.  Not to be called while the handle is in
+ * use on a stream.
+ */
+int syk_terms_replan(syk_terms_t* h, size_t l2_budget_bytes, double straggler_ratio);
 /*
  * Copy the compiled table to HOST arrays of length info.n_terms (any may be
  * NULL): flip mask x, sign mask z, coefficient per block (coef_U, coef_D)

@@ -16,7 +16,8 @@ SYK_OTOC_TYPICAL, SYK_OTOC_EXACT_TRACE = 0, 1
 class TermsInfo(C.Structure):
     _fields_ = [("N", C.c_int), ("L", C.c_int), ("dtype", C.c_int), ("rep", C.c_int), ("D", C.c_int64),
                 ("n_input", C.c_int64), ("n_terms", C.c_int64), ("n_real", C.c_int64),
-                ("n_xgroups", C.c_int64), ("sum_abs_coef", C.c_double)]
+                ("n_xgroups", C.c_int64), ("sum_abs_coef", C.c_double), ("n_passes", C.c_int64),
+                ("device_error", C.c_int64)]
 
 
 class KrylovParams(C.Structure):
@@ -35,6 +36,7 @@ SIGNATURES = {
     "syk_build_terms": (_I, [_I, _I64, _P, _P, _I, _I, C.POINTER(_P)]),
     "syk_terms_destroy": (_I, [_P]),
     "syk_terms_get_info": (_I, [_P, C.POINTER(TermsInfo)]),
+    "syk_terms_replan": (_I, [_P, _SZ, _D]),
     "syk_terms_export": (_I, [_P, _P, _P, _P, _P, _P]),
     "syk_compile_terms_host": (_I, [_I, _I64, _P, _P, _I, _I64, C.POINTER(_I64), _P, _P, _P, _P, _P]),
     "syk_compile_chi_host": (_I, [_I, _I, _I, _P, _P, _P, _P]),

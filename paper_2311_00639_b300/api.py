@@ -130,6 +130,20 @@ class Terms:
             raise ValueError("tensor size is not a multiple of D")
         return t.numel() // self.D
 
+    def device_error(self) -> int:
+        """1 if a kernel on this handle hit its bounded-wait limit (synchronises)."""
+        info = L.TermsInfo()
+        L.check(self._lib.syk_terms_get_info(self._h, C.byref(info)))
+        return int(info.device_error)
+
+    def replan(self, l2_budget_bytes: int = 2 << 20, straggler_ratio: float = 1.5):
+        """Regroup the matvec passes (L2 budget in bytes, straggler cost ratio)."""
+        L.check(self._lib.syk_terms_replan(self._h, int(l2_budget_bytes), float(straggler_ratio)))
+        info = L.TermsInfo()
+        L.check(self._lib.syk_terms_get_info(self._h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in L.TermsInfo._fields_}
+        return self.info["n_passes"]
+
     def export(self) -> dict:
         n = self.n_terms
         out = {"x": np.zeros(n, np.uint32), "z": np.zeros(n, np.uint32), "coef_U": np.zeros(n),

@@ -17,6 +17,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -80,6 +83,8 @@ enum { EPI_STORE = 0, EPI_LANCZOS = 1, EPI_RECUR = 2 };
 template <typename Real>
 struct MV {
   TermsView<Real> tv;
+  const PassPlan* pass;  // device pointer to this launch's pass
+  const TermF* rec;      // complex64: packed (x, z, c) records of the block being applied
   const typename CT<Real>::T* psi;
   typename CT<Real>::T* out;
   uint64_t D;
@@ -101,11 +106,14 @@ __device__ __forceinline__ C lanczos_w1(Real ar, Real ai, Real bprev, C vp) {
   return w;
 }
 
-template <typename Real, int R, int EPI>
+// ACCUM: add the partial sum already in `out` (passes after the first).  The
+// Lanczos epilogues run only in the last pass of a launch sequence.
+template <typename Real, int R, int EPI, bool ACCUM>
 __global__ void __launch_bounds__(256) k_matvec(MV<Real> p) {
   using C = typename CT<Real>::T;
   if (EPI == EPI_LANCZOS && p.sc->m_eff <= p.j) return;
   if (EPI == EPI_RECUR && p.j + 1 >= p.sc->m_eff) return;
+  const int t0 = p.pass->t0, ti = p.pass->ti, t1 = p.pass->t1;
   const uint64_t soff = static_cast<uint64_t>(blockIdx.y) * p.D;
   const C* __restrict__ psi = p.psi + soff;
   C* __restrict__ out = p.out + soff;
@@ -124,11 +132,16 @@ __global__ void __launch_bounds__(256) k_matvec(MV<Real> p) {
   }
   double part = 0.0;
   for (uint32_t bt = blockIdx.x; bt < ntiles; bt += gridDim.x) {
-    const uint32_t base = bt * tile + warp * 32u * R;
+    // R == 8 tiles are 2^kTileBits amplitudes placed by the pass's deposit tables
+    // (super-tile order); smaller vectors use the plain order.
+    const uint32_t tb = (R == 8) ? (__ldg(&p.pass->dep[0][bt & 255u]) | __ldg(&p.pass->dep[1][(bt >> 8) & 255u]) |
+                                    __ldg(&p.pass->dep[2][(bt >> 16) & 255u]))
+                                 : bt * tile;
+    const uint32_t base = tb + warp * 32u * R;
     Real ar[R], ai[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) ar[r] = ai[r] = Real(0);
-    for (int t = 0; t < p.tv.n_real; ++t) {
+    for (int t = t0; t < ti; ++t) {
       const uint32_t x = __ldg(p.tv.x + t), z = __ldg(p.tv.z + t);
       const Real cl = sgnflip(__ldg(p.tv.coef + t), __popc(z & lane) & 1u);
       const uint32_t off = lane ^ (x & 31u), xh = x & ~31u;
@@ -141,7 +154,7 @@ __global__ void __launch_bounds__(256) k_matvec(MV<Real> p) {
         ai[r] = fma_(cc, v.y, ai[r]);
       }
     }
-    for (int t = p.tv.n_real; t < p.tv.n; ++t) {  // coefficient i * c
+    for (int t = ti; t < t1; ++t) {  // coefficient i * c
       const uint32_t x = __ldg(p.tv.x + t), z = __ldg(p.tv.z + t);
       const Real cl = sgnflip(__ldg(p.tv.coef + t), __popc(z & lane) & 1u);
       const uint32_t off = lane ^ (x & 31u), xh = x & ~31u;
@@ -157,6 +170,11 @@ __global__ void __launch_bounds__(256) k_matvec(MV<Real> p) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t m = base + 32u * r + lane;
+      if (ACCUM) {
+        const C prev = out[m];
+        ar[r] += prev.x;
+        ai[r] += prev.y;
+      }
       if (EPI == EPI_STORE) {
         C o;
         o.x = ar[r];
@@ -189,6 +207,474 @@ __global__ void __launch_bounds__(256) k_matvec(MV<Real> p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged matvec for vectors of at least one 2^kTileBits tile.
+//
+// A CTA (8 warps) owns a 2048-amplitude output tile at a time.  For a term
+// with flip mask x the whole input tile T ^ (x & ~2047) is contiguous, so one
+// elected thread moves it into shared memory with a single bulk copy
+// (cp.async.bulk, completion counted on an mbarrier).  S stages keep S-1
+// copies in flight ahead of the consumers, which read their permuted
+// amplitudes from shared memory (x & 2047 permutes inside the tile; the XOR
+// keeps each warp's 32 reads in 32 distinct 8-byte slots, conflict-free).
+// One __syncthreads per term releases the stage that the next copy reuses.
+// Every mbarrier wait is bounded (1 s of %globaltimer); a timeout records an
+// error flag and the CTA drains and exits instead of spinning forever.
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// L2 eviction-priority policies (createpolicy) for bulk copies and stores.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
+                                              uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void st_f4_hint(float4* ptr, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
+
+// Bounded wait; returns false (and sets *s_err) on timeout or if another
+// thread already recorded an error.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int* s_err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t_start = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*s_err) return false;
+    if (globaltimer_ns() - t_start > kWaitLimitNs) {
+      *s_err = 1;
+      return false;
+    }
+  }
+}
+
+template <typename Real, int S>
+struct TmaSmem {
+  static constexpr uint32_t kTileAmps = 1u << kTileBits;
+  static constexpr uint32_t kTileBytes = kTileAmps * 2 * sizeof(Real);
+  static constexpr size_t kDynBytes = static_cast<size_t>(S) * kTileBytes;
+};
+
+template <typename Real, int EPI, bool ACCUM, int S>
+__global__ void __launch_bounds__(256) k_matvec_tma(MV<Real> p, int* err_flag) {
+  using C = typename CT<Real>::T;
+  constexpr uint32_t kTileBytes = TmaSmem<Real, S>::kTileBytes;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ int s_err;
+  if (EPI == EPI_LANCZOS && p.sc->m_eff <= p.j) return;
+  if (EPI == EPI_RECUR && p.j + 1 >= p.sc->m_eff) return;
+  const int t0 = p.pass->t0, ti = p.pass->ti, t1 = p.pass->t1;
+  const int Tp = t1 - t0;
+  const uint64_t soff = static_cast<uint64_t>(blockIdx.y) * p.D;
+  const C* __restrict__ psi = p.psi + soff;
+  C* __restrict__ out = p.out + soff;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t ntiles = static_cast<uint32_t>(p.D >> kTileBits);
+  const uint32_t my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x - 1) / gridDim.x + 1 : 0;
+  const uint64_t njobs = static_cast<uint64_t>(my_tiles) * static_cast<uint64_t>(Tp);
+  const uint32_t smem0 = smem_u32(smem_raw);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) mbar_init(smem_u32(&full_bar[i]), 1);
+    s_err = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto tile_base = [&](uint32_t k) -> uint32_t {
+    const uint32_t bt = blockIdx.x + k * gridDim.x;
+    return __ldg(&p.pass->dep[0][bt & 255u]) | __ldg(&p.pass->dep[1][(bt >> 8) & 255u]) |
+           __ldg(&p.pass->dep[2][(bt >> 16) & 255u]);
+  };
+  // Job j = (tile k = j / Tp, term t0 + j % Tp) goes to stage j % S.
+  auto issue = [&](uint64_t j) {
+    const uint32_t k = static_cast<uint32_t>(j / Tp);
+    const int tt = t0 + static_cast<int>(j % Tp);
+    const uint32_t src = tile_base(k) ^ (__ldg(p.tv.x + tt) & ~((1u << kTileBits) - 1u));
+    const uint32_t stg = static_cast<uint32_t>(j % S);
+    const uint32_t bar = smem_u32(&full_bar[stg]);
+    mbar_expect_tx(bar, kTileBytes);
+    bulk_g2s(smem0 + stg * kTileBytes, psi + src, kTileBytes, bar);
+  };
+  uint64_t issued = 0;       // thread 0: jobs whose copy has been issued
+  uint64_t first_fail = ~0ull;  // thread 0: first job it could not wait for
+  if (threadIdx.x == 0)
+    for (; issued + 1 < S && issued < njobs; ++issued) issue(issued);
+
+  Real bprev = 0, alpha = 0, rbeta = 0;
+  C cy = {0, 0};
+  if (EPI != EPI_STORE && p.j > 0) bprev = static_cast<Real>(p.sc->beta[p.j - 1]);
+  if (EPI == EPI_RECUR) {
+    alpha = static_cast<Real>(p.sc->alpha[p.j]);
+    rbeta = static_cast<Real>(1.0 / p.sc->beta[p.j]);
+    cy.x = static_cast<Real>(p.sc->beta0 * p.sc->c_re[p.j + 1]);
+    cy.y = static_cast<Real>(p.sc->beta0 * p.sc->c_im[p.j + 1]);
+  }
+  double part = 0.0;
+  uint64_t j = 0;
+  for (uint32_t k = 0; k < my_tiles; ++k) {
+    const uint32_t base = tile_base(k) + warp * 256u;
+    Real ar[8], ai[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) ar[r] = ai[r] = Real(0);
+    for (int tt = t0; tt < t1; ++tt, ++j) {
+      if (threadIdx.x == 0 && j + S - 1 < njobs && !s_err) {
+        fence_proxy_async_smem();
+        issue(j + S - 1);
+        issued = j + S;
+      }
+      const uint32_t stg = static_cast<uint32_t>(j % S);
+      const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), static_cast<uint32_t>((j / S) & 1), &s_err);
+      if (!ok && threadIdx.x == 0 && first_fail == ~0ull) first_fail = j;
+      if (ok) {
+        const C* tile = reinterpret_cast<const C*>(smem_raw + stg * kTileBytes);
+        const uint32_t x = __ldg(p.tv.x + tt), z = __ldg(p.tv.z + tt);
+        const Real cl = sgnflip(__ldg(p.tv.coef + tt), __popc(z & lane) & 1u);
+        const uint32_t off = lane ^ (x & 31u), xr = x & 0x7E0u;
+        if (tt < ti) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const Real cc = sgnflip(cl, __popc(z & (base + 32u * r)) & 1u);
+            const C v = tile[((warp * 256u + 32u * r) ^ xr) | off];
+            ar[r] = fma_(cc, v.x, ar[r]);
+            ai[r] = fma_(cc, v.y, ai[r]);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const Real cc = sgnflip(cl, __popc(z & (base + 32u * r)) & 1u);
+            const C v = tile[((warp * 256u + 32u * r) ^ xr) | off];
+            ar[r] = fma_(-cc, v.y, ar[r]);
+            ai[r] = fma_(cc, v.x, ai[r]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint32_t m = base + 32u * r + lane;
+      if (ACCUM) {
+        const C prev = out[m];
+        ar[r] += prev.x;
+        ai[r] += prev.y;
+      }
+      if (EPI == EPI_STORE) {
+        C o;
+        o.x = ar[r];
+        o.y = ai[r];
+        out[m] = o;
+      } else {
+        C vp = {0, 0};
+        if (p.j > 0) vp = p.vprev[soff + m];
+        const C w1 = lanczos_w1<Real, C>(ar[r], ai[r], bprev, vp);
+        const C v = psi[m];
+        if (EPI == EPI_LANCZOS) {
+          out[m] = w1;
+          part += static_cast<double>(v.x * w1.x + v.y * w1.y);
+        } else {
+          C vn;
+          vn.x = mul_(fma_(-alpha, v.x, w1.x), rbeta);
+          vn.y = mul_(fma_(-alpha, v.y, w1.y), rbeta);
+          out[m] = vn;
+          C yy = p.y[soff + m];
+          yy.x = fma_(cy.x, vn.x, fma_(-cy.y, vn.y, yy.x));
+          yy.y = fma_(cy.x, vn.y, fma_(cy.y, vn.x, yy.y));
+          p.y[soff + m] = yy;
+        }
+      }
+    }
+  }
+  if (EPI == EPI_LANCZOS) {
+    part = block_sum(part);
+    if (threadIdx.x == 0) p.partial[blockIdx.y * gridDim.x + blockIdx.x] = part;
+  }
+  if (s_err && threadIdx.x == 0) {
+    // Drain: wait (bounded) for every copy issued after the first job thread 0
+    // could not wait for, so no bulk copy is still writing when the CTA exits.
+    atomicExch(err_flag, 1);
+    for (uint64_t q = first_fail; q < issued; ++q) {
+      const uint32_t bar = smem_u32(&full_bar[q % S]);
+      const uint64_t ts = globaltimer_ns();
+      while (!mbar_try_wait(bar, static_cast<uint32_t>((q / S) & 1)) && globaltimer_ns() - ts < kWaitLimitNs) {
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// complex64 matvec, warp-specialised TMA pipeline (vectors of >= 2048 amplitudes).
+//
+// Warp 8 is the producer: its lane 0 streams input tiles (one 16 KiB bulk
+// copy per (tile, term) job) into S shared-memory stages, waiting on an
+// "empty" mbarrier per stage before reusing it.  Warps 0-7 consume: each
+// lane owns two neighbouring amplitudes in four rows of its warp's 256-
+// amplitude slice (m = tile + 256 w + 64 r + 2 lane + {0, 1}), reads both
+// inputs of a term with one 16-byte shared load, and signals the stage free
+// with one arrive per warp.  Terms of a pass are sorted by class
+// (imag, x & 1, z & 1) so that the pair swap (x & 1) and the sign difference
+// inside the pair (z & 1) are compile-time; the row permutation (bits 6-7 of
+// x) is a warp-uniform switch.  Every wait is bounded (1 s); on a timeout the
+// CTA records the error, stops issuing, drains its copies and exits.
+constexpr int kConsumerWarps = 8;
+constexpr int kStagesC64 = 4;
+
+template <bool IMAG, bool XS, bool ZS, int XR>
+__device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t pa2, const float c[4],
+                                         float (&a)[4][4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const float4 v = t4[pa2 + 32u * static_cast<uint32_t>(r ^ XR)];
+    // inputs of amplitude m (even) and m + 1
+    const float i0r = XS ? v.z : v.x, i0i = XS ? v.w : v.y;
+    const float i1r = XS ? v.x : v.z, i1i = XS ? v.y : v.w;
+    const float c0 = c[r];
+    const float c1 = ZS ? -c[r] : c[r];
+    if (!IMAG) {
+      a[r][0] = fma_(c0, i0r, a[r][0]);
+      a[r][1] = fma_(c0, i0i, a[r][1]);
+      a[r][2] = fma_(c1, i1r, a[r][2]);
+      a[r][3] = fma_(c1, i1i, a[r][3]);
+    } else {  // (i c) * v = c * (-v.im, v.re)
+      a[r][0] = fma_(-c0, i0i, a[r][0]);
+      a[r][1] = fma_(c0, i0r, a[r][1]);
+      a[r][2] = fma_(-c1, i1i, a[r][2]);
+      a[r][3] = fma_(c1, i1r, a[r][3]);
+    }
+  }
+}
+
+template <bool IMAG, bool XS, bool ZS, int S>
+__device__ __forceinline__ void c64_consume(int tb0, int tb1, uint64_t& q, float (&a)[4][4],
+                                            const TermF* __restrict__ rec, uint32_t mt, uint32_t pair_part,
+                                            const unsigned char* smem, uint64_t* full_bar, uint64_t* empty_bar,
+                                            volatile int* s_err, uint32_t lane) {
+  for (int tt = tb0; tt < tb1; ++tt, ++q) {
+    const uint32_t stg = static_cast<uint32_t>(q % S);
+    const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), static_cast<uint32_t>((q / S) & 1), s_err);
+    if (ok) {
+      const uint4 d = __ldg(reinterpret_cast<const uint4*>(rec + tt));
+      const uint32_t x = d.x, z = d.y;
+      const float cf = __uint_as_float(d.z);
+      const uint32_t sl = __popc(z & mt) & 1u;
+      const uint32_t zr = (z >> 6) & 3u;
+      const uint32_t s1 = sl ^ (zr & 1u), s2 = sl ^ (zr >> 1);
+      const float c[4] = {sgnflip(cf, sl), sgnflip(cf, s1), sgnflip(cf, s2), sgnflip(cf, s1 ^ (zr >> 1))};
+      const uint32_t pa2 = (pair_part ^ (x & 0x73Eu)) >> 1;  // float4 index of the row-0 input pair
+      const float4* t4 = reinterpret_cast<const float4*>(smem + stg * (1u << kTileBits) * 8u);
+      switch ((x >> 6) & 3u) {
+        case 0: c64_rows<IMAG, XS, ZS, 0>(t4, pa2, c, a); break;
+        case 1: c64_rows<IMAG, XS, ZS, 1>(t4, pa2, c, a); break;
+        case 2: c64_rows<IMAG, XS, ZS, 2>(t4, pa2, c, a); break;
+        default: c64_rows<IMAG, XS, ZS, 3>(t4, pa2, c, a); break;
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && ok) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty_bar[stg])) : "memory");
+  }
+}
+
+template <int EPI, bool ACCUM, int S>
+__global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 3) k_matvec_c64(MV<float> p, int* err_flag) {
+  constexpr uint32_t kTileBytes = (1u << kTileBits) * 8u;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ int s_err;
+  if (EPI == EPI_LANCZOS && p.sc->m_eff <= p.j) return;
+  if (EPI == EPI_RECUR && p.j + 1 >= p.sc->m_eff) return;
+  int cls[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) cls[c] = p.pass->cls[c];
+  const int t0 = cls[0], t1 = cls[8];
+  const int Tp = t1 - t0;
+  const uint64_t soff = static_cast<uint64_t>(blockIdx.y) * p.D;
+  const float2* __restrict__ psi = p.psi + soff;
+  float2* __restrict__ out = p.out + soff;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t ntiles = static_cast<uint32_t>(p.D >> kTileBits);
+  const uint32_t my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x - 1) / gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(smem_u32(&full_bar[i]), 1);
+      mbar_init(smem_u32(&empty_bar[i]), kConsumerWarps);
+    }
+    s_err = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto tile_base = [&](uint32_t k) -> uint32_t {
+    const uint32_t bt = blockIdx.x + k * gridDim.x;
+    return __ldg(&p.pass->dep[0][bt & 255u]) | __ldg(&p.pass->dep[1][(bt >> 8) & 255u]) |
+           __ldg(&p.pass->dep[2][(bt >> 16) & 255u]);
+  };
+  double part = 0.0;
+  if (warp == kConsumerWarps) {
+    // ---------------- producer ----------------
+    if (lane == 0 && (Tp > 0 || ACCUM)) {
+      const uint32_t smem0 = smem_u32(smem_raw);
+      const uint64_t keep = l2_policy_evict_last();   // input tiles: re-read by the pass's other terms
+      const uint64_t stream = l2_policy_evict_first();  // the output tile: read once per pass
+      uint64_t q = 0, issued = 0;
+      // Job stream per tile: [the tile of `out` (ACCUM only)] then one input tile per term.
+      for (uint32_t k = 0; k < my_tiles && !*(volatile int*)&s_err; ++k) {
+        const uint32_t tb = tile_base(k);
+        for (int tt = ACCUM ? t0 - 1 : t0; tt < t1 && !*(volatile int*)&s_err; ++tt, ++q) {
+          const uint32_t stg = static_cast<uint32_t>(q % S);
+          if (q >= S && !mbar_wait_bounded(smem_u32(&empty_bar[stg]), static_cast<uint32_t>(((q / S) - 1) & 1),
+                                           &s_err))
+            break;
+          const bool phi = ACCUM && tt < t0;
+          const uint2 xf = phi ? make_uint2(0u, 0u) : make_uint2(__ldg(&p.rec[tt].x), __ldg(&p.rec[tt].flags));
+          const float2* src = phi ? out + tb : psi + (tb ^ (xf.x & ~((1u << kTileBits) - 1u)));
+          const uint32_t bar = smem_u32(&full_bar[stg]);
+          mbar_expect_tx(bar, kTileBytes);
+          bulk_g2s_hint(smem0 + stg * kTileBytes, src, kTileBytes, bar, (phi || (xf.y & 1u)) ? stream : keep);
+          issued = q + 1;
+        }
+      }
+      if (s_err) {  // drain: the last copy issued into each stage must land before exit
+        for (uint64_t qq = issued > S ? issued - S : 0; qq < issued; ++qq) {
+          const uint32_t bar = smem_u32(&full_bar[qq % S]);
+          const uint64_t ts = globaltimer_ns();
+          while (!mbar_try_wait(bar, static_cast<uint32_t>((qq / S) & 1)) && globaltimer_ns() - ts < kWaitLimitNs) {
+          }
+        }
+      }
+    }
+  } else {
+    // ---------------- consumers ----------------
+    float bprev = 0.f, alpha = 0.f, rbeta = 0.f;
+    float2 cy = {0.f, 0.f};
+    if (EPI != EPI_STORE && p.j > 0) bprev = static_cast<float>(p.sc->beta[p.j - 1]);
+    if (EPI == EPI_RECUR) {
+      alpha = static_cast<float>(p.sc->alpha[p.j]);
+      rbeta = static_cast<float>(1.0 / p.sc->beta[p.j]);
+      cy.x = static_cast<float>(p.sc->beta0 * p.sc->c_re[p.j + 1]);
+      cy.y = static_cast<float>(p.sc->beta0 * p.sc->c_im[p.j + 1]);
+    }
+    const uint32_t pair_part = warp * 256u + 2u * lane;
+    const uint64_t out_pol = l2_policy_evict_first();  // output tiles are not re-read within the pass
+    const float4* psi4 = reinterpret_cast<const float4*>(psi);
+    float4* out4 = reinterpret_cast<float4*>(out);
+    uint64_t q = 0;
+    for (uint32_t k = 0; k < my_tiles; ++k) {
+      const uint32_t mt = tile_base(k) + pair_part;  // amplitude of row 0, even
+      float4 prev[4];
+      if (ACCUM) {  // the producer's first job of the tile is this tile of `out`
+        const uint32_t stg = static_cast<uint32_t>(q % S);
+        const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), static_cast<uint32_t>((q / S) & 1), &s_err);
+        const float4* t4 = reinterpret_cast<const float4*>(smem_raw + stg * kTileBytes);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) prev[r] = ok ? t4[(pair_part >> 1) + 32u * r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+        if (lane == 0 && ok)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty_bar[stg])) : "memory");
+        ++q;
+      }
+      float a[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
+      c64_consume<false, false, false, S>(cls[0], cls[1], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<false, false, true, S>(cls[1], cls[2], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<false, true, false, S>(cls[2], cls[3], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<false, true, true, S>(cls[3], cls[4], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<true, false, false, S>(cls[4], cls[5], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<true, false, true, S>(cls[5], cls[6], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<true, true, false, S>(cls[6], cls[7], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<true, true, true, S>(cls[7], cls[8], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t i4 = (mt >> 1) + 32u * r;
+        if (ACCUM) {
+          a[r][0] += prev[r].x;
+          a[r][1] += prev[r].y;
+          a[r][2] += prev[r].z;
+          a[r][3] += prev[r].w;
+        }
+        if (EPI == EPI_STORE) {
+          st_f4_hint(out4 + i4, make_float4(a[r][0], a[r][1], a[r][2], a[r][3]), out_pol);
+        } else {
+          float4 vp = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (p.j > 0) vp = reinterpret_cast<const float4*>(p.vprev + soff)[i4];
+          const float2 w0 = lanczos_w1<float, float2>(a[r][0], a[r][1], bprev, make_float2(vp.x, vp.y));
+          const float2 w1 = lanczos_w1<float, float2>(a[r][2], a[r][3], bprev, make_float2(vp.z, vp.w));
+          const float4 v = psi4[i4];
+          if (EPI == EPI_LANCZOS) {
+            out4[i4] = make_float4(w0.x, w0.y, w1.x, w1.y);
+            part += static_cast<double>(v.x * w0.x + v.y * w0.y) + static_cast<double>(v.z * w1.x + v.w * w1.y);
+          } else {
+            float4 vn;
+            vn.x = mul_(fma_(-alpha, v.x, w0.x), rbeta);
+            vn.y = mul_(fma_(-alpha, v.y, w0.y), rbeta);
+            vn.z = mul_(fma_(-alpha, v.z, w1.x), rbeta);
+            vn.w = mul_(fma_(-alpha, v.w, w1.y), rbeta);
+            out4[i4] = vn;
+            float4* y4 = reinterpret_cast<float4*>(p.y + soff);
+            float4 yy = y4[i4];
+            yy.x = fma_(cy.x, vn.x, fma_(-cy.y, vn.y, yy.x));
+            yy.y = fma_(cy.x, vn.y, fma_(cy.y, vn.x, yy.y));
+            yy.z = fma_(cy.x, vn.z, fma_(-cy.y, vn.w, yy.z));
+            yy.w = fma_(cy.x, vn.w, fma_(cy.y, vn.z, yy.w));
+            y4[i4] = yy;
+          }
+        }
+      }
+    }
+  }
+  if (EPI == EPI_LANCZOS) {
+    part = block_sum(part);
+    if (threadIdx.x == 0) p.partial[blockIdx.y * gridDim.x + blockIdx.x] = part;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_err) atomicExch(err_flag, 1);
+}
+
 // D < 32: one thread per amplitude, one warp.
 template <typename Real, int EPI>
 __global__ void k_matvec_tiny(MV<Real> p) {
@@ -199,13 +685,14 @@ __global__ void k_matvec_tiny(MV<Real> p) {
   const C* psi = p.psi + soff;
   const uint32_t m = threadIdx.x;
   double part = 0.0;
+  const int t0 = p.pass->t0, ti = p.pass->ti, t1 = p.pass->t1;
   if (m < p.D) {
     Real ar = 0, ai = 0;
-    for (int t = 0; t < p.tv.n; ++t) {
+    for (int t = t0; t < t1; ++t) {
       const uint32_t x = p.tv.x[t], z = p.tv.z[t];
       const Real cc = sgnflip(p.tv.coef[t], __popc(z & m) & 1u);
       const C v = psi[m ^ x];
-      if (t < p.tv.n_real) {
+      if (t < ti) {
         ar = fma_(cc, v.x, ar);
         ai = fma_(cc, v.y, ai);
       } else {
@@ -545,46 +1032,98 @@ TermsView<Real> view(const syk_terms* h, int block) {
   v.x = h->d_x;
   v.z = h->d_z;
   v.coef = static_cast<const Real*>(h->d_coef[block]);
-  v.n_real = static_cast<int>(h->n_real);
-  v.n = static_cast<int>(h->terms.size());
   return v;
 }
 
 struct Shape {
-  int R, warps, grid;
+  int R, warps, grid;  // R == 8: TMA-staged 2048-amplitude tiles
 };
+
+constexpr int kStagesF = 4;  // complex64: 4 x 16 KiB in flight per CTA
+constexpr int kStagesD = 3;  // complex128: 3 x 32 KiB
+
+template <typename Real>
+constexpr int stages() {
+  return sizeof(Real) == 4 ? kStagesF : kStagesD;
+}
 
 Shape shape_of(const syk_terms* h) {
   Shape s;
   const uint64_t D = static_cast<uint64_t>(h->D);
   if (D < 32) return {0, 1, 1};
-  if (D >= 2048) {
+  const uint64_t ntiles_cap = static_cast<uint64_t>(h->n_sm);
+  if (D >= (1ull << kTileBits)) {
     s.R = 8;
     s.warps = 8;
-  } else {
-    s.R = 1;
-    s.warps = static_cast<int>(std::min<uint64_t>(8, D / 32));
+    // CTAs resident per SM given the stage buffers (3 for complex64, 2 for complex128).
+    const uint64_t per_sm = h->dtype == SYK_C128 ? 2 : 3;
+    s.grid = static_cast<int>(std::min<uint64_t>(D >> kTileBits, ntiles_cap * per_sm));
+    return s;
   }
+  s.R = 1;
+  s.warps = static_cast<int>(std::min<uint64_t>(8, D / 32));
   const uint64_t ntiles = D / (32ull * s.R * s.warps);
-  s.grid = static_cast<int>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(h->n_sm) * 8));
+  s.grid = static_cast<int>(std::min<uint64_t>(ntiles, ntiles_cap * 8));
   return s;
 }
 
+template <typename Real, int EPI, bool ACCUM>
+void launch_pass(const syk_terms* h, const Shape& s, const MV<Real>& q, unsigned gy, cudaStream_t st) {
+  if constexpr (std::is_same<Real, float>::value) {
+    if (s.R == 8) {
+      constexpr size_t dyn = static_cast<size_t>(kStagesC64) * (1u << kTileBits) * 8u;
+      static std::atomic<uint64_t> configured{0};
+      const uint64_t bit = 1ull << (h->device & 63);
+      if (!(configured.load() & bit)) {
+        SYK_CUDA(cudaFuncSetAttribute(k_matvec_c64<EPI, ACCUM, kStagesC64>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn)));
+        configured.fetch_or(bit);
+      }
+      k_matvec_c64<EPI, ACCUM, kStagesC64><<<dim3(s.grid, gy), 32 * (kConsumerWarps + 1), dyn, st>>>(q, h->d_err);
+      return;
+    }
+  }
+  if (s.R == 8) {
+    constexpr int S = stages<Real>();
+    constexpr size_t dyn = TmaSmem<Real, S>::kDynBytes;
+    static std::atomic<uint64_t> configured{0};  // one bit per device ordinal (< 64)
+    const uint64_t bit = 1ull << (h->device & 63);
+    if (!(configured.load() & bit)) {
+      SYK_CUDA(cudaFuncSetAttribute(k_matvec_tma<Real, EPI, ACCUM, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(dyn)));
+      configured.fetch_or(bit);
+    }
+    k_matvec_tma<Real, EPI, ACCUM, S><<<dim3(s.grid, gy), 256, dyn, st>>>(q, h->d_err);
+  } else {
+    k_matvec<Real, 1, EPI, ACCUM><<<dim3(s.grid, gy), 32 * s.warps, 0, st>>>(q);
+  }
+}
+
+// One launch per pass: passes before the last write (first) or accumulate
+// plain partial sums; the last pass applies the requested epilogue.
 template <typename Real, int EPI>
 void run_matvec(const syk_terms* h, const MV<Real>& p, int64_t nstates, cudaStream_t st) {
   const Shape s = shape_of(h);
+  const int np = static_cast<int>(h->passes.size());
   for (int64_t s0 = 0; s0 < nstates; s0 += 65535) {
     MV<Real> q = p;
     const uint64_t off = static_cast<uint64_t>(s0) * h->D;
     q.psi += off;
     q.out += off;
     const unsigned gy = static_cast<unsigned>(std::min<int64_t>(65535, nstates - s0));
-    if (s.R == 0) {
+    if (s.R == 0) {  // single pass
+      q.pass = h->d_passes;
       k_matvec_tiny<Real, EPI><<<dim3(1, gy), 32, 0, st>>>(q);
-    } else if (s.R == 8) {
-      k_matvec<Real, 8, EPI><<<dim3(s.grid, gy), 32 * s.warps, 0, st>>>(q);
-    } else {
-      k_matvec<Real, 1, EPI><<<dim3(s.grid, gy), 32 * s.warps, 0, st>>>(q);
+      continue;
+    }
+    for (int ip = 0; ip < np; ++ip) {
+      q.pass = h->d_passes + ip;
+      const bool last = ip == np - 1, accum = ip > 0;
+      if (!last)
+        accum ? launch_pass<Real, EPI_STORE, true>(h, s, q, gy, st)
+              : launch_pass<Real, EPI_STORE, false>(h, s, q, gy, st);
+      else
+        accum ? launch_pass<Real, EPI, true>(h, s, q, gy, st) : launch_pass<Real, EPI, false>(h, s, q, gy, st);
     }
   }
   SYK_CUDA(cudaGetLastError());
@@ -614,6 +1153,7 @@ void launch_apply_H(const syk_terms* h, int block, const void* psi, void* out, i
     using C = typename CT<Real>::T;
     MV<Real> p{};
     p.tv = view<Real>(h, block);
+    p.rec = h->d_termf[block];
     p.psi = static_cast<const C*>(psi);
     p.out = static_cast<C*>(out);
     p.D = static_cast<uint64_t>(h->D);
@@ -676,6 +1216,7 @@ void launch_lanczos_matvec(const syk_terms* h, int block, const void* v, const v
     using C = typename CT<Real>::T;
     MV<Real> p{};
     p.tv = view<Real>(h, block);
+    p.rec = h->d_termf[block];
     p.psi = static_cast<const C*>(v);
     p.out = static_cast<C*>(w);
     p.vprev = static_cast<const C*>(vprev);
@@ -751,6 +1292,7 @@ void launch_lanczos_recur(const syk_terms* h, int block, const void* v, const vo
     using C = typename CT<Real>::T;
     MV<Real> p{};
     p.tv = view<Real>(h, block);
+    p.rec = h->d_termf[block];
     p.psi = static_cast<const C*>(v);
     p.out = static_cast<C*>(vnext);
     p.vprev = static_cast<const C*>(vprev);

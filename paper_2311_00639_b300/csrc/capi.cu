@@ -82,6 +82,71 @@ Params resolve(const syk_terms* h, const syk_krylov_params* p) {
 
 }  // namespace
 
+namespace {
+void upload_table(syk_terms* h) {
+    const size_t n = h->terms.size();
+    const size_t rb = h->dtype == SYK_C128 ? 8 : 4;
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const size_t pass_bytes = up(h->passes.size() * sizeof(syk::PassPlan));
+    const size_t rec_bytes = up(std::max<size_t>(n, 1) * sizeof(syk::TermF));
+    const size_t bytes =
+        2 * up(std::max<size_t>(n, 1) * 4) + 2 * up(std::max<size_t>(n, 1) * rb) + pass_bytes + 256 + 2 * rec_bytes;
+    std::vector<char> host(bytes, 0);
+    char* p = host.data();
+    uint32_t* hx = reinterpret_cast<uint32_t*>(p);
+    uint32_t* hz = reinterpret_cast<uint32_t*>(p + up(std::max<size_t>(n, 1) * 4));
+    char* hc0 = p + 2 * up(std::max<size_t>(n, 1) * 4);
+    char* hc1 = hc0 + up(std::max<size_t>(n, 1) * rb);
+    char* hp = hc1 + up(std::max<size_t>(n, 1) * rb);
+    std::memcpy(hp, h->passes.data(), h->passes.size() * sizeof(syk::PassPlan));
+    char* hr0 = hp + pass_bytes + 256;
+    char* hr1 = hr0 + rec_bytes;
+    for (size_t i = 0; i < n; ++i)
+      for (int b = 0; b < 2; ++b) {
+        syk::TermF r;
+        r.x = h->terms[i].x;
+        r.z = h->terms[i].z;
+        r.c = static_cast<float>(h->terms[i].coef[b]);
+        r.flags = h->terms[i].straggler ? 1u : 0u;
+        std::memcpy((b ? hr1 : hr0) + i * sizeof(syk::TermF), &r, sizeof(r));
+      }
+    for (size_t i = 0; i < n; ++i) {
+      hx[i] = h->terms[i].x;
+      hz[i] = h->terms[i].z;
+      for (int b = 0; b < 2; ++b) {
+        char* dst = (b ? hc1 : hc0) + i * rb;
+        if (h->dtype == SYK_C128) {
+          const double v = h->terms[i].coef[b];
+          std::memcpy(dst, &v, 8);
+        } else {
+          const float v = static_cast<float>(h->terms[i].coef[b]);
+          std::memcpy(dst, &v, 4);
+        }
+      }
+    }
+    if (h->d_mem) {
+      SYK_CUDA(cudaDeviceSynchronize());
+      cudaFree(h->d_mem);
+      h->d_mem = nullptr;
+    }
+    if (cudaMalloc(&h->d_mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw syk::Error(SYK_ENOMEM, "device allocation of the term table failed");
+    }
+    SYK_CUDA(cudaMemcpy(h->d_mem, host.data(), bytes, cudaMemcpyHostToDevice));
+    char* d = static_cast<char*>(h->d_mem);
+    h->d_x = reinterpret_cast<uint32_t*>(d);
+    h->d_z = reinterpret_cast<uint32_t*>(d + (reinterpret_cast<char*>(hz) - p));
+    h->d_coef[0] = d + (hc0 - p);
+    h->d_coef[1] = d + (hc1 - p);
+    h->d_passes = reinterpret_cast<syk::PassPlan*>(d + (hp - p));
+    h->d_err = reinterpret_cast<int*>(d + (hp - p) + pass_bytes);  // zeroed with the host image
+    h->d_termf[0] = reinterpret_cast<syk::TermF*>(d + (hr0 - p));
+    h->d_termf[1] = reinterpret_cast<syk::TermF*>(d + (hr1 - p));
+}
+
+}  // namespace
+
 namespace syk {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace syk
@@ -117,42 +182,10 @@ int syk_build_terms(int N, int64_t T, const int32_t* quads, const double* J, int
     syk::compile_terms(N, rep, T, quads, J, h->terms, h->n_real, h->n_xgroups);
     for (const auto& t : h->terms) h->sum_abs += std::max(std::fabs(t.coef[0]), std::fabs(t.coef[1]));
     for (int n = 0; n < N; ++n) h->chi[n] = syk::compile_chi(N, rep, n);
+    h->passes = syk::plan_passes(h->terms, h->L, syk::elem_bytes(dtype), syk::kL2Budget, syk::kDefaultHbmRatio);
     SYK_CUDA(cudaGetDevice(&h->device));
     SYK_CUDA(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device));
-    const size_t n = h->terms.size();
-    const size_t rb = dtype == SYK_C128 ? 8 : 4;
-    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-    const size_t bytes = 2 * up(std::max<size_t>(n, 1) * 4) + 2 * up(std::max<size_t>(n, 1) * rb);
-    std::vector<char> host(bytes, 0);
-    char* p = host.data();
-    uint32_t* hx = reinterpret_cast<uint32_t*>(p);
-    uint32_t* hz = reinterpret_cast<uint32_t*>(p + up(std::max<size_t>(n, 1) * 4));
-    char* hc0 = p + 2 * up(std::max<size_t>(n, 1) * 4);
-    char* hc1 = hc0 + up(std::max<size_t>(n, 1) * rb);
-    for (size_t i = 0; i < n; ++i) {
-      hx[i] = h->terms[i].x;
-      hz[i] = h->terms[i].z;
-      for (int b = 0; b < 2; ++b) {
-        char* dst = (b ? hc1 : hc0) + i * rb;
-        if (dtype == SYK_C128) {
-          const double v = h->terms[i].coef[b];
-          std::memcpy(dst, &v, 8);
-        } else {
-          const float v = static_cast<float>(h->terms[i].coef[b]);
-          std::memcpy(dst, &v, 4);
-        }
-      }
-    }
-    if (cudaMalloc(&h->d_mem, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      throw syk::Error(SYK_ENOMEM, "device allocation of the term table failed");
-    }
-    SYK_CUDA(cudaMemcpy(h->d_mem, host.data(), bytes, cudaMemcpyHostToDevice));
-    char* d = static_cast<char*>(h->d_mem);
-    h->d_x = reinterpret_cast<uint32_t*>(d);
-    h->d_z = reinterpret_cast<uint32_t*>(d + (reinterpret_cast<char*>(hz) - p));
-    h->d_coef[0] = d + (hc0 - p);
-    h->d_coef[1] = d + (hc1 - p);
+    upload_table(h.get());
     *out = h.release();
   });
 }
@@ -176,6 +209,20 @@ int syk_terms_get_info(const syk_terms_t* h, syk_terms_info* info) {
     info->n_real = h->n_real;
     info->n_xgroups = h->n_xgroups;
     info->sum_abs_coef = h->sum_abs;
+    info->n_passes = static_cast<int64_t>(h->passes.size());
+    int e = 0;
+    SYK_CUDA(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    info->device_error = e;
+  });
+}
+
+int syk_terms_replan(syk_terms_t* h, size_t l2_budget_bytes, double straggler_ratio) {
+  return guarded("syk_terms_replan", [&] {
+    check_handle(h);
+    SYK_REQUIRE(l2_budget_bytes >= 4096, "l2_budget_bytes must be >= 4096");
+    SYK_REQUIRE(std::isfinite(straggler_ratio) && straggler_ratio >= 0, "straggler_ratio must be >= 0");
+    h->passes = syk::plan_passes(h->terms, h->L, syk::elem_bytes(h->dtype), l2_budget_bytes, straggler_ratio);
+    upload_table(h);
   });
 }
 

@@ -13,6 +13,8 @@
 namespace syk {
 
 constexpr int kMaxKrylov = 64;   // largest Krylov dimension per substep
+constexpr int kTileBits = 11;    // amplitudes per matvec block tile = 2^11 (8 warps x 8 rows x 32 lanes)
+constexpr size_t kL2Budget = size_t(2) << 20;  // default bytes of a block vector kept L2-resident per pass
 constexpr int kMaxPartials = 2048;  // per-state reduction partials (>= any grid.x)
 
 struct Error : std::runtime_error {
@@ -37,6 +39,7 @@ struct BlockString {
   uint32_t x = 0, z = 0;
   double coef[2] = {0.0, 0.0};  // block U, block D
   bool imag = false;
+  bool straggler = false;  // read from outside its pass's L2-resident super-tile
 };
 
 // A single Majorana restricted to block P -> 1-P, same output-index form,
@@ -54,14 +57,35 @@ ChiString compile_chi(int N, int rep, int n);
 // Record the message syk_last_error() returns on this thread (capi.cu).
 void set_last_error(const std::string& msg);
 
+// One pass of the blocked matvec (plan.cpp).  Terms [t0, ti) have a real
+// coefficient and [ti, t1) an imaginary one; tile index bt maps to the first
+// amplitude dep[0][bt & 255] | dep[1][(bt >> 8) & 255] | dep[2][(bt >> 16) & 255].
+// The same struct is copied to the device.
+struct PassPlan {
+  int t0 = 0, ti = 0, t1 = 0;
+  uint32_t emask = 0;  // bits held fixed within a super-tile
+  // Terms of class c = 4*imag + 2*(x & 1) + (z & 1) are [cls[c], cls[c+1]).
+  int cls[9] = {};
+  uint32_t dep[3][256] = {};
+};
+// Packed complex64 term record (one 16-byte load per term); flags bit 0 marks
+// a straggler (its input tiles come from HBM, fetched with evict-first).
+struct alignas(16) TermF {
+  uint32_t x, z;
+  float c;
+  uint32_t flags;
+};
+// Reorders `terms` by pass and returns the passes.
+std::vector<PassPlan> plan_passes(std::vector<BlockString>& terms, int L, size_t elem_bytes, size_t l2_budget,
+                                   double hbm_ratio);
+constexpr double kDefaultHbmRatio = 1.5;  // best of a B300 sweep at N = 64 (budget x ratio grid)
+
 // Device view of a compiled term table, in compute precision Real.
 template <typename Real>
 struct TermsView {
   const uint32_t* x;
   const uint32_t* z;
   const Real* coef;  // coefficients of the block being applied
-  int n_real;        // terms [0, n_real) real, [n_real, n) imaginary
-  int n;
 };
 
 }  // namespace syk
@@ -77,6 +101,10 @@ struct syk_terms {
   uint32_t* d_x = nullptr;
   uint32_t* d_z = nullptr;
   void* d_coef[2] = {nullptr, nullptr};
+  std::vector<syk::PassPlan> passes;
+  syk::PassPlan* d_passes = nullptr;
+  syk::TermF* d_termf[2] = {nullptr, nullptr};  // complex64 handles: packed terms per block
+  int* d_err = nullptr;  // set by a kernel whose bounded wait expired
   int n_sm = 148;
   syk_terms() = default;
   syk_terms(const syk_terms&) = delete;

@@ -84,6 +84,44 @@ def test_apply_H_N32_vs_csr(syk, dtype):
             assert rel_err(got, ref) < TOL_H[dtype]
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_apply_H_multipass_plans_N32(syk, dtype):
+    """Blocked passes (forced by small L2 budgets, down to the plain-order
+    fallback pass) give the same H psi as the oracle CSR matrix."""
+    N = 32
+    q, J, _ = si.sample_sparse_syk(N, 4, r=1)
+    psi = rand_vec(1 << 15, 2, n=2)
+    refs = [ham.csr_block(N, q, J, "jw", blk) @ psi.T for blk in (0, 1)]
+    with syk.Terms(N, q, J, dtype=dtype) as h:
+        assert h.info["n_passes"] == 1
+        seen = set()
+        for budget in (1 << 30, 1 << 16, 1 << 14, 4096):
+            npass = h.replan(budget)
+            seen.add(npass)
+            ex = h.export()
+            assert len(ex["x"]) == h.n_terms
+            for blk in (0, 1):
+                got = h.apply_H(to_dev(psi, dtype), blk).cpu().numpy()
+                assert rel_err(got, refs[blk].T) < TOL_H[dtype], (budget, npass)
+        assert max(seen) >= 2
+        assert h.device_error() == 0
+
+
+def test_krylov_multipass_N32(syk):
+    """Fused Lanczos epilogues on the last pass of a multi-pass matvec."""
+    N = 32
+    q, J, _ = si.sample_sparse_syk(N, 4, r=12)
+    Hc = ham.csr_block(N, q, J, "jw", 0)
+    x = rand_vec(1 << 15, 14)
+    ref = dyn.evolve_sparse(Hc, 0.5 + 2.0j, x)
+    with syk.Terms(N, q, J, dtype="c128") as h:
+        h.replan(1 << 16)
+        assert h.info["n_passes"] >= 2
+        for two_pass in (False, True):
+            y, _ = h.krylov_evolve(to_dev(x, "c128"), 0, 0.5, 2.0, tol=1e-13, two_pass=two_pass)
+            assert rel_err(y.cpu().numpy(), ref) < 1e-10
+
+
 def test_apply_H_dense_syk_and_empty(syk):
     """Dense SYK (every quadruple, many terms share a flip mask) and H = 0."""
     N = 12
@@ -116,6 +154,7 @@ def test_apply_H_sampled_rows_large(syk, dtype, N):
             at = lambda b, m: si.philox_state(N, 77, 3, np.uint64(b * D) + m)
             ref = ham.rows_of_Hpsi(N, q, J, "jw", blk, rows, at)
             assert rel_err(got, ref) < (2e-5 if dtype == "c64" else 1e-12)
+        assert h.device_error() == 0
         del psiU, psiD
         t.cuda.empty_cache()
 
