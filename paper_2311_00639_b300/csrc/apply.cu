@@ -245,6 +245,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait with a suspend-time hint: the thread may sleep in hardware until
+// the phase completes or about `ns` nanoseconds pass, instead of spinning.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
@@ -285,7 +298,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t_start = globaltimer_ns();
   for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;  // sleep up to 0.1 ms per try
     if (*s_err) return false;
     if (globaltimer_ns() - t_start > kWaitLimitNs) {
       *s_err = 1;
@@ -462,7 +475,13 @@ __global__ void __launch_bounds__(256) k_matvec_tma(MV<Real> p, int* err_flag) {
 // x) is a warp-uniform switch.  Every wait is bounded (1 s); on a timeout the
 // CTA records the error, stops issuing, drains its copies and exits.
 constexpr int kConsumerWarps = 8;
-constexpr int kStagesC64 = 4;
+#ifndef SYK_C64_STAGES
+#define SYK_C64_STAGES 4
+#endif
+constexpr int kStagesC64 = SYK_C64_STAGES;
+// CTAs per SM: shared memory holds S 16 KiB stages each (<= 227 KiB per SM);
+// 72 registers x 288 threads allow at most 3.
+constexpr int kC64CtasPerSm = (227 / (16 * kStagesC64 + 2)) < 3 ? (227 / (16 * kStagesC64 + 2)) : 3;
 
 template <bool IMAG, bool XS, bool ZS, int XR>
 __device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t pa2, const float c[4],
@@ -520,7 +539,7 @@ __device__ __forceinline__ void c64_consume(int tb0, int tb1, uint64_t& q, float
 }
 
 template <int EPI, bool ACCUM, int S>
-__global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 3) k_matvec_c64(MV<float> p, int* err_flag) {
+__global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_matvec_c64(MV<float> p, int* err_flag) {
   constexpr uint32_t kTileBytes = (1u << kTileBits) * 8u;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[S];
@@ -1055,8 +1074,8 @@ Shape shape_of(const syk_terms* h) {
   if (D >= (1ull << kTileBits)) {
     s.R = 8;
     s.warps = 8;
-    // CTAs resident per SM given the stage buffers (3 for complex64, 2 for complex128).
-    const uint64_t per_sm = h->dtype == SYK_C128 ? 2 : 3;
+    // CTAs resident per SM given the stage buffers.
+    const uint64_t per_sm = h->dtype == SYK_C128 ? 2 : static_cast<uint64_t>(kC64CtasPerSm);
     s.grid = static_cast<int>(std::min<uint64_t>(D >> kTileBits, ntiles_cap * per_sm));
     return s;
   }
