@@ -49,7 +49,8 @@ enum {
   SYK_ENOMEM = -2,   /* device or host allocation failed */
   SYK_ENOCONV = -3,  /* Krylov substep control did not converge */
   SYK_ETIMEOUT = -4, /* a bounded device wait expired */
-  SYK_ECUDA = -5     /* CUDA runtime error */
+  SYK_ECUDA = -5,    /* CUDA runtime error */
+  SYK_EAGAIN = -6    /* no free slot or memory right now (batched engine); retry later */
 };
 enum { SYK_C64 = 0, SYK_C128 = 1 };
 enum { SYK_REP_JW = 0, SYK_REP_PAPER = 1 };
@@ -238,6 +239,49 @@ int syk_krylov_evolve_noalloc(const syk_terms_t* h, int block, double tau, doubl
 int syk_otoc(const syk_terms_t* h, int a, int b, double beta, const double* t_grid, int n_t, int mode,
              int n_states, uint64_t seed, const void* psi_opt, const syk_krylov_params* p, double* F_raw,
              double* otoc, syk_krylov_stats* stats, syk_stream_t stream);
+
+/*
+ * Batched OTOC engine — many (realisation, state) OTOC curves at once.
+ * Each job is the typical-state OTOC of syk_otoc for one Hamiltonian handle
+ * (any N, same dtype as the batch), one Philox state (syk_random_state(seed,
+ * state_id), normalised over both blocks) and its own beta and time grid.  A
+ * job occupies a slot and device memory from the batch's arena
+ * ((m + 5) block vectors plus the grid; syk_batch_job_bytes) until it
+ * finishes; jobs of different N share every launch.  One tick advances every
+ * live job by one Krylov substep; the tick is a captured CUDA graph (Lanczos
+ * kernels batched over jobs, a per-job device state machine for the
+ * elementwise steps), so the host only admits and collects.  Lanczos uses a
+ * stored basis (no two_pass / reorth).
+ */
+typedef struct syk_batch syk_batch_t;
+typedef struct {
+  const syk_terms_t* h;      /* Hamiltonian (kept alive by the caller until the job finishes) */
+  int a, b;                  /* Majoranas of the OTOC */
+  double beta;
+  const double* t_grid;      /* HOST [n_t], non-decreasing; copied at submit */
+  int n_t;
+  uint64_t seed, state_id;   /* typical state */
+  int64_t tag;               /* caller's id, reported back when the job finishes */
+  double* F_out;             /* HOST [n_t][2] (re, im of F(t)), written when the job finishes */
+  syk_krylov_stats* stats;   /* HOST, optional */
+  int* status_out;           /* HOST, optional: SYK_OK or SYK_ENOCONV when the job finishes */
+} syk_otoc_job;
+/* max_bytes: device arena for job state (allocated once); max_slots: jobs in flight. */
+int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylov_params* p, syk_batch_t** out);
+int syk_batch_destroy(syk_batch_t* batch);
+/* Admit a job; SYK_EAGAIN if no slot or no arena range is free (retry after a run). */
+int syk_batch_submit(syk_batch_t* batch, const syk_otoc_job* job);
+/*
+ * Run ticks on the batch's own stream, synchronising every ticks_per_sync
+ * ticks, until at least one job finishes or max_ticks ticks have run.  Writes
+ * the finished jobs' outputs, frees their slots and memory, and reports how
+ * many finished (and up to max_finished of their tags).  Blocking.
+ */
+int syk_batch_run(syk_batch_t* batch, int max_ticks, int ticks_per_sync, int* n_finished, int64_t* finished_tags,
+                  int max_finished);
+int syk_batch_info(const syk_batch_t* batch, int* live_jobs, size_t* bytes_in_use, size_t* bytes_free_max);
+/* Device bytes a job needs (0 on bad arguments). */
+size_t syk_batch_job_bytes(const syk_batch_t* batch, const syk_terms_t* h, int n_t);
 
 /* Message of the last failing call on this thread (always NUL-terminated). */
 int syk_last_error(char* buf, size_t n);

@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsyk.so")
 
-SYK_OK, SYK_EINVAL, SYK_ENOMEM, SYK_ENOCONV, SYK_ETIMEOUT, SYK_ECUDA = 0, -1, -2, -3, -4, -5
+SYK_OK, SYK_EINVAL, SYK_ENOMEM, SYK_ENOCONV, SYK_ETIMEOUT, SYK_ECUDA, SYK_EAGAIN = 0, -1, -2, -3, -4, -5, -6
 SYK_C64, SYK_C128 = 0, 1
 SYK_REP_JW, SYK_REP_PAPER = 0, 1
 SYK_OTOC_TYPICAL, SYK_OTOC_EXACT_TRACE = 0, 1
@@ -27,6 +27,12 @@ class KrylovParams(C.Structure):
 
 class KrylovStats(C.Structure):
     _fields_ = [("matvecs", C.c_int64), ("substeps", C.c_int64), ("err_est", C.c_double)]
+
+
+class OtocJob(C.Structure):
+    _fields_ = [("h", C.c_void_p), ("a", C.c_int), ("b", C.c_int), ("beta", C.c_double), ("t_grid", C.c_void_p),
+                ("n_t", C.c_int), ("seed", C.c_uint64), ("state_id", C.c_uint64), ("tag", C.c_int64),
+                ("F_out", C.c_void_p), ("stats", C.c_void_p), ("status_out", C.c_void_p)]
 
 
 # name -> (restype, argtypes); every symbol include/syk.h declares.
@@ -50,6 +56,12 @@ SIGNATURES = {
                                        C.POINTER(KrylovStats), _P]),
     "syk_otoc": (_I, [_P, _I, _I, _D, _P, _I, _I, _I, _U64, _P, C.POINTER(KrylovParams), _P, _P,
                       C.POINTER(KrylovStats), _P]),
+    "syk_batch_create": (_I, [_I, _I, _SZ, C.POINTER(KrylovParams), C.POINTER(_P)]),
+    "syk_batch_destroy": (_I, [_P]),
+    "syk_batch_submit": (_I, [_P, C.POINTER(OtocJob)]),
+    "syk_batch_run": (_I, [_P, _I, _I, C.POINTER(_I), _P, _I]),
+    "syk_batch_info": (_I, [_P, C.POINTER(_I), C.POINTER(_SZ), C.POINTER(_SZ)]),
+    "syk_batch_job_bytes": (_SZ, [_P, _P, _I]),
     "syk_last_error": (_I, [C.c_char_p, _SZ]),
     "syk_version": (C.c_char_p, []),
 }

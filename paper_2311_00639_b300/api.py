@@ -234,3 +234,86 @@ class Terms:
                                    C.c_uint64(seed), None if psi is None else _ptr(psi), C.byref(p),
                                    F.ctypes.data, o.ctypes.data, C.byref(st), _stream(stream)))
         return F[..., 0] + 1j * F[..., 1], o, KrylovStats(st)
+
+
+class Batch:
+    """Batched OTOC engine (syk_batch_*): many typical-state OTOC curves at once.
+
+    submit() admits a job if a slot and arena memory are free (returns False
+    otherwise); run() advances all live jobs and returns the finished ones as
+    dicts {tag, F (complex [n_t]), otoc (normalised), matvecs, substeps, status}.
+    """
+
+    def __init__(self, dtype: str = "c64", max_slots: int = 64, max_bytes: int = 1 << 30, m: int = 30, tol=None):
+        self._lib = L.load()
+        h = C.c_void_p()
+        p = _params(m=m, tol=tol)
+        L.check(self._lib.syk_batch_create(_DT[dtype], int(max_slots), int(max_bytes), C.byref(p), C.byref(h)))
+        self._h = h
+        self.dtype = dtype
+        self._pending = {}  # tag -> (F buffer, stats, status, t_grid, terms)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.syk_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def job_bytes(self, terms: "Terms", n_t: int) -> int:
+        return int(self._lib.syk_batch_job_bytes(self._h, terms._h, int(n_t)))
+
+    def submit(self, terms: "Terms", a: int, b: int, beta: float, t_grid, seed: int, state_id: int, tag: int) -> bool:
+        if terms.dtype != self.dtype:
+            raise ValueError("terms dtype differs from the batch dtype")
+        tg = np.ascontiguousarray(np.asarray(t_grid, dtype=np.float64))
+        F = np.zeros((len(tg), 2))
+        st = L.KrylovStats()
+        status = C.c_int(0)
+        job = L.OtocJob(terms._h, int(a), int(b), float(beta), tg.ctypes.data, len(tg), C.c_uint64(seed),
+                        C.c_uint64(state_id), int(tag), F.ctypes.data, C.addressof(st), C.addressof(status))
+        rc = self._lib.syk_batch_submit(self._h, C.byref(job))
+        if rc == L.SYK_EAGAIN:
+            return False
+        L.check(rc)
+        self._pending[int(tag)] = (F, st, status, tg, terms)
+        return True
+
+    def run(self, max_ticks: int = 1 << 20, ticks_per_sync: int = 8):
+        n = C.c_int(0)
+        cap = max(1, len(self._pending))
+        tags = (C.c_int64 * cap)()
+        L.check(self._lib.syk_batch_run(self._h, int(max_ticks), int(ticks_per_sync), C.byref(n), tags, cap))
+        out = []
+        for i in range(min(n.value, cap)):
+            F, st, status, tg, _ = self._pending.pop(int(tags[i]))
+            Fc = F[:, 0] + 1j * F[:, 1]
+            out.append({"tag": int(tags[i]), "F": Fc, "otoc": Fc.real / Fc.real[0], "matvecs": st.matvecs,
+                        "substeps": st.substeps, "status": status.value})
+        return out
+
+    def info(self) -> dict:
+        live, used, free = C.c_int(0), C.c_size_t(0), C.c_size_t(0)
+        L.check(self._lib.syk_batch_info(self._h, C.byref(live), C.byref(used), C.byref(free)))
+        return {"live": live.value, "bytes_in_use": used.value, "largest_free": free.value}
+
+    @property
+    def pending(self) -> int:
+        return len(self._pending)
+
+    def drain(self, max_ticks: int = 1 << 20, ticks_per_sync: int = 8):
+        """Run until every admitted job has finished; returns all results."""
+        out = []
+        while self._pending:
+            out += self.run(max_ticks, ticks_per_sync)
+        return out

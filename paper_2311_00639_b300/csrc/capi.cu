@@ -89,8 +89,9 @@ void upload_table(syk_terms* h) {
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
     const size_t pass_bytes = up(h->passes.size() * sizeof(syk::PassPlan));
     const size_t rec_bytes = up(std::max<size_t>(n, 1) * sizeof(syk::TermF));
-    const size_t bytes =
-        2 * up(std::max<size_t>(n, 1) * 4) + 2 * up(std::max<size_t>(n, 1) * rb) + pass_bytes + 256 + 2 * rec_bytes;
+    const size_t zi_bytes = up(std::max<size_t>(n, 1) * 4);
+    const size_t bytes = 2 * up(std::max<size_t>(n, 1) * 4) + 2 * up(std::max<size_t>(n, 1) * rb) + pass_bytes + 256 +
+                         2 * rec_bytes + zi_bytes;
     std::vector<char> host(bytes, 0);
     char* p = host.data();
     uint32_t* hx = reinterpret_cast<uint32_t*>(p);
@@ -101,6 +102,8 @@ void upload_table(syk_terms* h) {
     std::memcpy(hp, h->passes.data(), h->passes.size() * sizeof(syk::PassPlan));
     char* hr0 = hp + pass_bytes + 256;
     char* hr1 = hr0 + rec_bytes;
+    uint32_t* hzi = reinterpret_cast<uint32_t*>(hr1 + rec_bytes);
+    for (size_t i = 0; i < n; ++i) hzi[i] = h->terms[i].z | (h->terms[i].imag ? 0x80000000u : 0u);
     for (size_t i = 0; i < n; ++i)
       for (int b = 0; b < 2; ++b) {
         syk::TermF r;
@@ -143,6 +146,7 @@ void upload_table(syk_terms* h) {
     h->d_err = reinterpret_cast<int*>(d + (hp - p) + pass_bytes);  // zeroed with the host image
     h->d_termf[0] = reinterpret_cast<syk::TermF*>(d + (hr0 - p));
     h->d_termf[1] = reinterpret_cast<syk::TermF*>(d + (hr1 - p));
+    h->d_zi = reinterpret_cast<uint32_t*>(d + (reinterpret_cast<char*>(hzi) - p));
 }
 
 }  // namespace

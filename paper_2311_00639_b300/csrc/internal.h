@@ -105,6 +105,7 @@ struct syk_terms {
   syk::PassPlan* d_passes = nullptr;
   syk::TermF* d_termf[2] = {nullptr, nullptr};  // complex64 handles: packed terms per block
   int* d_err = nullptr;  // set by a kernel whose bounded wait expired
+  uint32_t* d_zi = nullptr;  // z | (imag << 31) per term (batched engine)
   int n_sm = 148;
   syk_terms() = default;
   syk_terms(const syk_terms&) = delete;

@@ -1,0 +1,121 @@
+"""Batched OTOC engine (syk_batch_*) against the single-realisation path and
+the CPU oracle; mixed sizes, admission back-pressure, and "alone == in the
+mix" (bitwise, since every job's arithmetic is independent of the others)."""
+import numpy as np
+import pytest
+
+import syk_inputs as si
+from oracle import hamiltonian as ham
+from oracle import majorana as mj
+from oracle import otoc as ot
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def syk():
+    import paper_2311_00639_b300 as p
+
+    return p
+
+
+def philox_normed(N, seed, sid):
+    v = si.philox_state(N, seed, sid)
+    v = v / np.linalg.norm(v)
+    D = len(v) // 2
+    return v[:D], v[D:]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_batch_matches_oracle_and_single_path(syk, dtype):
+    N = 12
+    rep = "jw"
+    q, J, _ = si.sample_sparse_syk(N, 4, r=21)
+    H = ham.dense_H(N, q, J, rep)
+    HU, HD = ham.blocks(H, N, rep)
+    X = mj.chis(N, rep)
+    ts = np.array([0.0, 0.5, 1.5, 3.0])
+    tol = 1e-10 if dtype == "c128" else 2e-4
+    with syk.Terms(N, q, J, dtype=dtype, rep=rep) as h, syk.Batch(dtype=dtype, max_slots=8, max_bytes=64 << 20) as b:
+        jobs = [(N - 1, N - 2, 5.0, 7, 0), (N - 1, N - 2, 0.0, 7, 1), (2, 9, 2.0, 11, 3)]
+        for tag, (a, bb, beta, seed, sid) in enumerate(jobs):
+            assert b.submit(h, a, bb, beta, ts, seed, sid, tag)
+        res = {r["tag"]: r for r in b.drain()}
+        assert len(res) == len(jobs)
+        for tag, (a, bb, beta, seed, sid) in enumerate(jobs):
+            r = res[tag]
+            assert r["status"] == 0 and r["matvecs"] > 0
+            pU, pD = philox_normed(N, seed, sid)
+            ref = ot.F_state_blocks(N, rep, HU, HD, X, a, bb, beta, ts, pU, pD)
+            assert np.max(np.abs(r["F"] - ref)) < tol, (tag, r["F"], ref)
+            if sid == 0:  # the single path generates state_id = 0 for its first state
+                F1, _, _ = h.otoc(a, bb, beta, ts, n_states=1, seed=seed)
+                assert np.max(np.abs(r["F"] - F1[0])) < tol
+
+
+def test_batch_mixed_sizes_and_backpressure(syk):
+    """Jobs of N = 10..26 share launches; only 3 slots, so admission waits."""
+    ts = np.array([0.0, 1.0, 2.0])
+    sizes = [10, 14, 18, 22, 26, 12, 20, 16]
+    handles = []
+    with syk.Batch(dtype="c128", max_slots=3, max_bytes=256 << 20) as b:
+        for N in sizes:
+            q, J, _ = si.sample_sparse_syk(N, 4, r=N)
+            handles.append(syk.Terms(N, q, J, dtype="c128"))
+        waiting = list(range(len(sizes)))
+        results = {}
+        refused = 0
+        while waiting or b.pending:
+            while waiting:
+                i = waiting[0]
+                if not b.submit(handles[i], sizes[i] - 1, sizes[i] - 2, 4.0, ts, 99, i, i):
+                    refused += 1
+                    break
+                waiting.pop(0)
+            assert b.info()["live"] <= 3
+            for r in b.run():
+                results[r["tag"]] = r
+        assert refused > 0 and len(results) == len(sizes)
+        for i, N in enumerate(sizes):
+            F1, _, _ = handles[i].otoc(N - 1, N - 2, 4.0, ts, n_states=1, seed=99)
+            # the batch used state_id = i; regenerate the single-path reference with that state
+            pU, pD = philox_normed(N, 99, i)
+            psi = np.stack([np.stack([pU, pD])])
+            import torch
+
+            Fs, _, _ = handles[i].otoc(N - 1, N - 2, 4.0, ts, psi=torch.from_numpy(psi).cuda())
+            assert np.max(np.abs(results[i]["F"] - Fs[0])) < 1e-10, N
+    for h in handles:
+        h.close()
+
+
+def test_batch_alone_equals_in_mix_bitwise(syk):
+    ts = np.array([0.0, 0.7, 2.1])
+    N = 18
+    q, J, _ = si.sample_sparse_syk(N, 4, r=5)
+    q2, J2, _ = si.sample_sparse_syk(24, 4, r=6)
+    with syk.Terms(N, q, J, dtype="c64") as h, syk.Terms(24, q2, J2, dtype="c64") as h2:
+        with syk.Batch(dtype="c64", max_slots=4, max_bytes=256 << 20) as b:
+            assert b.submit(h, N - 1, N - 2, 5.0, ts, 3, 0, 0)
+            alone = b.drain()[0]["F"]
+        with syk.Batch(dtype="c64", max_slots=6, max_bytes=256 << 20) as b:
+            assert b.submit(h2, 23, 22, 10.0, [0.0, 4.0, 8.0], 5, 1, 10)
+            assert b.submit(h, N - 1, N - 2, 5.0, ts, 3, 0, 0)
+            assert b.submit(h2, 1, 7, 2.0, ts, 5, 2, 11)
+            mixed = {r["tag"]: r["F"] for r in b.drain()}[0]
+    assert np.array_equal(alone, mixed)
+
+
+def test_batch_arena_refuses_beyond_budget(syk):
+    N = 26
+    q, J, _ = si.sample_sparse_syk(N, 4, r=1)
+    with syk.Terms(N, q, J, dtype="c128") as h, syk.Batch(dtype="c128", max_slots=16, max_bytes=16 << 20) as b:
+        need = b.job_bytes(h, 3)
+        assert need > 0
+        admitted = 0
+        while b.submit(h, N - 1, N - 2, 1.0, [0.0, 1.0, 2.0], 1, admitted, admitted):
+            admitted += 1
+        assert admitted == (16 << 20) // need
+        assert b.info()["bytes_in_use"] == admitted * need
+        res = b.drain()
+        assert len(res) == admitted and b.info()["bytes_in_use"] == 0
