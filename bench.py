@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-l2", action="store_true")
+    ap.add_argument("--no-otoc", action="store_true", help="skip the batched / served OTOC legs")
+    ap.add_argument("--batch-realizations", type=int, default=32)
+    ap.add_argument("--batch-states", type=int, default=4)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-tmax", type=float, default=20.0)
+    ap.add_argument("--serve-dt", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -173,6 +179,98 @@ def measured_traffic(T, D):
         return rec["dram_bytes_per_matvec"] * (T * D) / (rec["terms"] * rec["D"])
     except Exception:
         return None
+
+
+# ------------------------------------------------------------- OTOC legs ----
+def otoc_batched(args, syk, si, torch, rank=0):
+    """Batched OTOC (bounded form of the 4096-realisation configuration):
+    R realisations, N uniform in {24,...,36}, k uniform in {1,2,4,8}, beta=10,
+    S typical states each, t = 0..10 in 10 segments, complex64 states with
+    FP64 Lanczos scalars.  Also times the plain FP64 single-realisation path
+    (syk_otoc, complex128) on the same first realisations and reports the
+    complex64-vs-complex128 OTOC difference."""
+    import numpy as np
+
+    rng = np.random.default_rng(4242 + rank)
+    R, S = args.batch_realizations, args.batch_states
+    grid = np.linspace(0.0, 10.0, 11)
+    beta = 10.0
+    reals = []
+    for r in range(R):
+        N = int(rng.choice(np.arange(24, 37, 2)))
+        k = float(rng.choice([1.0, 2.0, 4.0, 8.0]))
+        q, J, _ = si.sample_sparse_syk(N, k, seed=700_000 + 1000 * rank + r)
+        reals.append((N, q, J, syk.Terms(N, q, J, dtype="c64")))
+    jobs = [(r, s) for r in range(R) for s in range(S)]
+    b = syk.Batch(dtype="c64", max_slots=len(jobs), max_bytes=40 << 30, m=30)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    results = {}
+    queue = list(enumerate(jobs))
+    while queue or b.pending:
+        while queue:
+            tag, (r, s) = queue[0]
+            N, _, _, h = reals[r]
+            if not b.submit(h, N - 1, N - 2, beta, grid, 1234 + r, s, tag):
+                break
+            queue.pop(0)
+        for res in b.run(ticks_per_sync=16):
+            results[res["tag"]] = res
+    wall = time.perf_counter() - t0
+    termamps = sum(results[t]["matvecs"] * reals[jobs[t][0]][3].n_terms * reals[jobs[t][0]][3].D for t in results)
+    b.close()
+    out = {"workload": f"{R} realisations x {S} states, N in 24..36, k in 1,2,4,8, beta=10, 11 t-points, c64",
+           "realizations_per_s": R / wall, "curves_per_s": len(jobs) / wall, "wall_s": wall,
+           "matvec_Gtermamp_s": termamps / wall / 1e9, "failed": sum(1 for v in results.values() if v["status"])}
+    # plain FP64 single-realisation path (complex128, one realisation at a time)
+    nplain = min(2, R)
+    t0 = time.perf_counter()
+    diffs = []
+    for r in range(nplain):
+        N, q, J, h = reals[r]
+        with syk.Terms(N, q, J, dtype="c128") as h64:
+            for s in range(S):
+                u, d = h64.random_state(1234 + r, s)
+                nrm = torch.sqrt(torch.sum(torch.abs(u) ** 2) + torch.sum(torch.abs(d) ** 2))
+                psi = torch.stack([u / nrm, d / nrm]).unsqueeze(0).contiguous()
+                F64, _, _ = h64.otoc(N - 1, N - 2, beta, grid, psi=psi)
+                diffs.append(np.max(np.abs(results[r * S + s]["F"] - F64[0])) / np.max(np.abs(F64[0])))
+    plain_wall = time.perf_counter() - t0
+    out["plain_fp64_single_path"] = {"realizations_per_s": nplain / plain_wall, "realizations": nplain,
+                                     "note": "syk_otoc complex128, one realisation and state at a time"}
+    out["c64_vs_fp64_max_rel_F_diff"] = float(max(diffs)) if diffs else None
+    for r in reals:
+        r[3].close()
+    return out
+
+
+def otoc_served(args, syk, torch):
+    """Served configuration (bounded): Poisson requests with N in 28..48
+    weighted toward small N, k in {0.5,1,2,4}, beta in {2,5,10,20}; the arrival
+    rate is set to ~75% of the capacity measured by a closed-loop pass."""
+    from paper_2311_00639_b300 import serve
+
+    kw = dict(t_max=args.serve_tmax, dt=args.serve_dt)
+    n = args.serve_requests
+    # capacity: all requests present at t=0
+    cap_reqs = serve.served_workload(n, rate=1e9, seed=11, **kw)
+    srv = serve.OtocServer(dtype="c64", max_slots=256, hbm_budget_bytes=100 << 30, ticks_per_step=8)
+    t0 = time.perf_counter()
+    res = srv.run(cap_reqs)
+    cap = len(res) / (time.perf_counter() - t0)
+    srv.close()
+    rate = 0.75 * cap
+    reqs = serve.served_workload(n, rate=rate, seed=12, **kw)
+    srv = serve.OtocServer(dtype="c64", max_slots=256, hbm_budget_bytes=100 << 30, ticks_per_step=8)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    srv.close()
+    summ = serve.summarize(res, wall)
+    summ.update({"arrival_rate_per_s": rate, "closed_loop_capacity_per_s": cap,
+                 "workload": f"{n} Poisson requests, N 28..48 (P ~ 0.7^((N-28)/2)), k 0.5..4, beta 2..20, "
+                             f"t 0..{args.serve_tmax:g} step {args.serve_dt:g}, c64, HBM budget 100 GB"})
+    return summ
 
 
 # ------------------------------------------------------------------ ours ----
@@ -309,6 +407,13 @@ def ours(args):
             "frac_of_l2_resident": (T * D / per_step / 1e9) / l2res["value"] if l2res else None}
     roof["traffic"] = measured_traffic(T, D)
 
+    batched = served = None
+    if not args.no_otoc:
+        torch.cuda.empty_cache()
+        batched = otoc_batched(args, syk, si, torch, rank)
+        if rank == 0:
+            served = otoc_served(args, syk, torch)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, nrows, _, cores = oracle_rows_rate(args.N, args.k, seconds=12.0)
@@ -322,7 +427,7 @@ def ours(args):
                 "config": {**workload_config(args, T), "parallelism": f"replicas x{world}",
                            "matvec_passes": h.info["n_passes"]},
                 "gpu_launches": args.steps * h.info["n_passes"], "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "fp64": fp64, "clocks": clk, "gpu": props.name}
+                "fp64": fp64, "clocks": clk, "gpu": props.name, "otoc_batched": batched, "otoc_served": served}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -1,0 +1,148 @@
+"""Continuous-batching OTOC server over the batched engine (syk_batch_*).
+
+Requests (one disorder realisation each: N, k, beta, time grid, seeds) arrive
+over time.  The loop compiles each arriving request's Hamiltonian
+(syk_build_terms), admits it into the running batch as soon as a slot and
+enough arena memory are free (admission by device footprint), advances all
+admitted jobs a few ticks at a time, and retires finished ones — so requests
+that arrive while others are on the GPU join them at the next tick instead of
+waiting for a batch to drain.  Latency = completion time - arrival time.
+All compute runs in libsyk; this module only schedules.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+from .api import Batch, Terms
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float  # seconds from the start of the run
+    N: int
+    quads: np.ndarray
+    J: np.ndarray
+    beta: float
+    t_grid: np.ndarray
+    seed: int
+    state_id: int = 0
+    a: int = -1  # Majoranas (default N-1, N-2)
+    b: int = -2
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    N: int
+    F: np.ndarray
+    otoc: np.ndarray
+    arrival: float
+    admitted: float
+    done: float
+    matvecs: int
+    status: int
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 0) -> np.ndarray:
+    """Arrival times of n requests of a Poisson process of the given rate (1/s)."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
+def percentile(values, q: float) -> float:
+    v = np.sort(np.asarray(values, dtype=np.float64))
+    if len(v) == 0:
+        return float("nan")
+    k = (len(v) - 1) * q / 100.0
+    lo, hi = math.floor(k), math.ceil(k)
+    return float(v[lo] + (v[hi] - v[lo]) * (k - lo))
+
+
+class OtocServer:
+    """batch / make_terms can be injected (tests drive the scheduling with fakes)."""
+
+    def __init__(self, dtype: str = "c64", max_slots: int = 256, hbm_budget_bytes: int = 8 << 30, m: int = 30,
+                 tol=None, ticks_per_step: int = 4, batch=None, make_terms=None):
+        self.batch = batch if batch is not None else Batch(dtype=dtype, max_slots=max_slots,
+                                                           max_bytes=hbm_budget_bytes, m=m, tol=tol)
+        self.make_terms = make_terms if make_terms is not None else (
+            lambda r: Terms(r.N, r.quads, r.J, dtype=dtype))
+        self.ticks = ticks_per_step
+        self.live = {}  # rid -> (Request, Terms, admitted time)
+
+    def close(self):
+        for _, (_, h, _) in list(self.live.items()):
+            h.close()
+        self.live.clear()
+        self.batch.close()
+
+    def run(self, requests, clock=time.perf_counter, sleep=time.sleep):
+        """Serve the requests (arrival times in seconds from now); returns the
+        Results in completion order."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue = []  # arrived and compiled, waiting for admission (FIFO, no overtaking)
+        out = []
+        t0 = clock()
+        now = lambda: clock() - t0
+        i = 0
+        while i < len(pending) or queue or self.live:
+            t = now()
+            while i < len(pending) and pending[i].arrival <= t:
+                queue.append((pending[i], self.make_terms(pending[i])))
+                i += 1
+            while queue:
+                r, h = queue[0]
+                a = r.a if r.a >= 0 else r.N + r.a
+                b = r.b if r.b >= 0 else r.N + r.b
+                if not self.batch.submit(h, a, b, r.beta, r.t_grid, r.seed, r.state_id, r.rid):
+                    break
+                self.live[r.rid] = (r, h, now())
+                queue.pop(0)
+            if self.live:
+                for res in self.batch.run(max_ticks=self.ticks, ticks_per_sync=self.ticks):
+                    r, h, adm = self.live.pop(res["tag"])
+                    out.append(Result(r.rid, r.N, res["F"], res["otoc"], r.arrival, adm, now(), res["matvecs"],
+                                      res["status"]))
+                    h.close()
+            elif i < len(pending):
+                sleep(max(0.0, min(0.01, pending[i].arrival - now())))
+        return out
+
+
+def summarize(results, wall: float) -> dict:
+    lat = [r.latency for r in results]
+    return {"requests": len(results), "wall_s": wall, "realizations_per_s": len(results) / wall if wall > 0 else None,
+            "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
+            "mean_latency_s": float(np.mean(lat)) if lat else None,
+            "failed": sum(1 for r in results if r.status != 0)}
+
+
+def served_workload(n: int, rate: float, seed: int = 0, n_choices=(28, 30, 32, 34, 36, 38, 40, 42, 44, 46, 48),
+                    weight: float = 0.7, ks=(0.5, 1.0, 2.0, 4.0), betas=(2.0, 5.0, 10.0, 20.0), t_max: float = 20.0,
+                    dt: float = 0.1):
+    """The served configuration: N weighted toward small sizes (P(N) ~ weight^((N-28)/2)),
+    k and beta uniform over the listed values, t = 0..t_max step dt, Poisson arrivals."""
+    import syk_inputs as si
+
+    rng = np.random.default_rng(seed)
+    Ns = np.asarray(n_choices)
+    p = weight ** ((Ns - Ns[0]) / 2.0)
+    p /= p.sum()
+    arr = poisson_arrivals(n, rate, seed)
+    grid = np.round(np.arange(0.0, t_max + 1e-9, dt), 10)
+    reqs = []
+    for i in range(n):
+        N = int(rng.choice(Ns, p=p))
+        k = float(rng.choice(ks))
+        q, J, _ = si.sample_sparse_syk(N, k, seed=10_000 + seed * 100_000 + i)
+        reqs.append(Request(i, float(arr[i]), N, q, J, float(rng.choice(betas)), grid, seed=seed * 1_000_003 + i))
+    return reqs

@@ -1,0 +1,94 @@
+"""Host-side scheduling of the OTOC server, driven by a fake batch (no GPU):
+FIFO admission without overtaking, admission refused beyond slot/memory
+limits, every request completes once, latency accounting."""
+import numpy as np
+
+from paper_2311_00639_b300 import serve
+
+
+class FakeTerms:
+    closed = 0
+
+    def __init__(self, r):
+        self.N = r.N
+
+    def close(self):
+        FakeTerms.closed += 1
+
+
+class FakeBatch:
+    """Admits while slots and 'bytes' allow; a job finishes after `work` ticks."""
+
+    def __init__(self, slots, budget):
+        self.slots, self.budget, self.used = slots, budget, 0
+        self.live = {}  # tag -> [remaining ticks, bytes]
+        self.admitted_order = []
+        self.max_live = 0
+        self.clock = 0.0
+
+    def submit(self, h, a, b, beta, tg, seed, sid, tag):
+        need = 2 ** (h.N // 2)
+        if len(self.live) >= self.slots or self.used + need > self.budget:
+            return False
+        self.live[tag] = [len(tg), need]
+        self.used += need
+        self.admitted_order.append(tag)
+        self.max_live = max(self.max_live, len(self.live))
+        return True
+
+    def run(self, max_ticks, ticks_per_sync):
+        out = []
+        for _ in range(max_ticks):
+            self.clock += 1e-3
+            for tag in list(self.live):
+                self.live[tag][0] -= 1
+                if self.live[tag][0] <= 0:
+                    self.used -= self.live.pop(tag)[1]
+                    F = np.ones(3, dtype=complex)
+                    out.append({"tag": tag, "F": F, "otoc": F.real, "matvecs": 1, "status": 0})
+            if out:
+                break
+        return out
+
+    def close(self):
+        pass
+
+
+def test_fifo_admission_limits_and_latency():
+    reqs = [serve.Request(i, 0.0005 * i, 10 + 2 * (i % 4), None, None, 1.0, np.zeros(3 + i % 5), seed=i)
+            for i in range(40)]
+    fb = FakeBatch(slots=3, budget=2 ** 8)
+    t = [0.0]
+
+    def clock():
+        t[0] += 1e-4
+        return t[0]
+
+    srv = serve.OtocServer(batch=fb, make_terms=FakeTerms, ticks_per_step=2)
+    res = srv.run(reqs, clock=clock, sleep=lambda s: None)
+    assert sorted(r.rid for r in res) == list(range(40))  # each once
+    assert fb.admitted_order == sorted(fb.admitted_order)  # FIFO, no overtaking
+    assert fb.max_live <= 3 and fb.used == 0
+    assert all(r.done >= r.admitted >= r.arrival for r in res)
+    assert FakeTerms.closed == 40
+    s = serve.summarize(res, wall=t[0])
+    assert s["requests"] == 40 and s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+def test_poisson_and_percentiles():
+    arr = serve.poisson_arrivals(20000, rate=50.0, seed=1)
+    gaps = np.diff(np.concatenate([[0.0], arr]))
+    assert abs(gaps.mean() - 1 / 50.0) < 0.05 / 50.0 * 10
+    assert np.all(np.diff(arr) > 0)
+    assert serve.percentile([1, 2, 3, 4, 5], 50) == 3.0
+    assert serve.percentile([1, 2, 3, 4, 5], 100) == 5.0
+    assert abs(serve.percentile(np.arange(101), 99) - 99.0) < 1e-12
+
+
+def test_served_workload_distribution():
+    reqs = serve.served_workload(300, rate=10.0, seed=2, t_max=1.0, dt=0.5)
+    Ns = np.array([r.N for r in reqs])
+    assert Ns.min() >= 28 and Ns.max() <= 48 and np.all(Ns % 2 == 0)
+    assert np.mean(Ns == 28) > np.mean(Ns == 34) > 0  # weighted toward small N
+    assert {r.beta for r in reqs} <= {2.0, 5.0, 10.0, 20.0}
+    assert np.allclose(reqs[0].t_grid, [0.0, 0.5, 1.0])
