@@ -265,6 +265,8 @@ typedef struct {
   double* F_out;             /* HOST [n_t][2] (re, im of F(t)), written when the job finishes */
   syk_krylov_stats* stats;   /* HOST, optional */
   int* status_out;           /* HOST, optional: SYK_OK or SYK_ENOCONV when the job finishes */
+  int64_t basis_index;       /* < 0: typical state; else the basis state g = block*D + m of the
+                                full space (exact trace = sum of these jobs over g, divided by 2D) */
 } syk_otoc_job;
 /* max_bytes: device arena for job state (allocated once); max_slots: jobs in flight. */
 int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylov_params* p, syk_batch_t** out);

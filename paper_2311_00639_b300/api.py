@@ -273,7 +273,8 @@ class Batch:
     def job_bytes(self, terms: "Terms", n_t: int) -> int:
         return int(self._lib.syk_batch_job_bytes(self._h, terms._h, int(n_t)))
 
-    def submit(self, terms: "Terms", a: int, b: int, beta: float, t_grid, seed: int, state_id: int, tag: int) -> bool:
+    def submit(self, terms: "Terms", a: int, b: int, beta: float, t_grid, seed: int, state_id: int, tag: int,
+               basis_index: int = -1) -> bool:
         if terms.dtype != self.dtype:
             raise ValueError("terms dtype differs from the batch dtype")
         tg = np.ascontiguousarray(np.asarray(t_grid, dtype=np.float64))
@@ -281,7 +282,8 @@ class Batch:
         st = L.KrylovStats()
         status = C.c_int(0)
         job = L.OtocJob(terms._h, int(a), int(b), float(beta), tg.ctypes.data, len(tg), C.c_uint64(seed),
-                        C.c_uint64(state_id), int(tag), F.ctypes.data, C.addressof(st), C.addressof(status))
+                        C.c_uint64(state_id), int(tag), F.ctypes.data, C.addressof(st), C.addressof(status),
+                        int(basis_index))
         rc = self._lib.syk_batch_submit(self._h, C.byref(job))
         if rc == L.SYK_EAGAIN:
             return False
@@ -317,3 +319,25 @@ class Batch:
         while self._pending:
             out += self.run(max_ticks, ticks_per_sync)
         return out
+
+
+def exact_trace_otoc(terms: "Terms", pairs, beta: float, t_grid, max_slots: int = 4096, max_bytes: int = 8 << 30,
+                     m: int = 30, tol=None):
+    """Exact-trace OTOC of Eq. (2) for each (a, b) in pairs, by the batched
+    engine over all 2D basis states: F_tr(t) = sum_g F_{e_g}(t) / 2D.
+    Returns {(a, b): (F complex [n_t], otoc [n_t])}."""
+    D = terms.D
+    tg = np.asarray(t_grid, dtype=np.float64)
+    acc = {tuple(p): np.zeros(len(tg), dtype=np.complex128) for p in pairs}
+    jobs = [(p, g) for p in acc for g in range(2 * D)]
+    with Batch(dtype=terms.dtype, max_slots=min(max_slots, len(jobs)), max_bytes=max_bytes, m=m, tol=tol) as b:
+        i = 0
+        while i < len(jobs) or b.pending:
+            while i < len(jobs):
+                (pa, pb), g = jobs[i]
+                if not b.submit(terms, pa, pb, beta, tg, 0, 0, i, basis_index=g):
+                    break
+                i += 1
+            for r in b.run(ticks_per_sync=16):
+                acc[jobs[r["tag"]][0]] += r["F"]
+    return {p: (F / (2 * D), (F / (2 * D)).real / (F / (2 * D)).real[0]) for p, F in acc.items()}

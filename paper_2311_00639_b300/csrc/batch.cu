@@ -57,6 +57,7 @@ struct BSlot {
   const double* tg;  // device [n_t]
   double* F;         // device [n_t][2]
   uint64_t seed, state_id;
+  long long basis;  // < 0: Philox typical state; else basis state index g = block*D + m
   void* vec[4];  // u0, bra, k1, k2
   void* V;       // basis, (m+1) x D
   // state machine
@@ -173,7 +174,22 @@ __global__ void __launch_bounds__(kBlk) k_b_control(BatchArgs a) {
       __syncthreads();
     };
     const int stage = s.stage;
-    if (stage == S_INIT) {  // norm of the Philox state over both blocks
+    if (stage == S_INIT && s.basis >= 0) {  // basis state: already normalised
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s.n2 = 1.0;
+        s.part = 0;
+        s.stage = S_PART;
+      }
+      __syncthreads();
+    } else if (stage == S_PART && s.basis >= 0 && s.basis / s.D != static_cast<long long>(P)) {
+      __syncthreads();  // the basis state has no component in this block: F_P = 0
+      if (threadIdx.x == 0) {
+        s.part += 1;
+        s.stage = (s.part >= 2) ? S_DONE : S_PART;
+      }
+      __syncthreads();
+    } else if (stage == S_INIT) {  // norm of the Philox state over both blocks
       double acc = 0.0;
       for (uint64_t g2 = threadIdx.x; g2 < 2ull * s.D; g2 += blockDim.x) {
         const double2 v = philox_amp(g2, s.seed, s.state_id);
@@ -190,7 +206,9 @@ __global__ void __launch_bounds__(kBlk) k_b_control(BatchArgs a) {
       const double inv = 1.0 / sqrt(s.n2);
       C* u0 = mvec<Real>(s, 0);
       for (uint32_t m = threadIdx.x; m < s.D; m += blockDim.x) {
-        const double2 v = philox_amp(static_cast<uint64_t>(P) * s.D + m, s.seed, s.state_id);
+        const uint64_t gidx = static_cast<uint64_t>(P) * s.D + m;
+        const double2 v = s.basis >= 0 ? make_double2(static_cast<long long>(gidx) == s.basis ? 1.0 : 0.0, 0.0)
+                                       : philox_amp(gidx, s.seed, s.state_id);
         C o;
         o.x = static_cast<Real>(v.x * inv);
         o.y = static_cast<Real>(v.y * inv);
@@ -692,6 +710,8 @@ int syk_batch_submit(syk_batch_t* h, const syk_otoc_job* job) {
     s.n_t = job->n_t;
     s.seed = job->seed;
     s.state_id = job->state_id;
+    SYK_REQUIRE(job->basis_index < 2 * t->D, "basis_index out of range [0, 2D)");
+    s.basis = job->basis_index < 0 ? -1 : job->basis_index;
     for (int i = 0; i < 4; ++i) s.vec[i] = base + i * vb;
     s.V = base + 4 * vb;
     char* tail = base + (4 + b.m + 1) * vb;
