@@ -136,6 +136,55 @@ class Terms:
         L.check(self._lib.syk_terms_get_info(self._h, C.byref(info)))
         return int(info.device_error)
 
+    def autotune(self, budgets_mb=(0.5, 1.0, 2.0, 4.0, 8.0), ratios=(0.0, 1.5, 3.0), reps: int = 2, block: int = 0,
+                 cache_path=None) -> dict:
+        """Pick the matvec pass plan (L2 budget, straggler ratio) by timing
+        syk_apply_H on this Hamiltonian; keeps the fastest plan.  With
+        cache_path, the choice is stored per (term table, dtype, GPU) and reused."""
+        import hashlib
+        import json
+        import os
+
+        torch = _torch()
+        ex = self.export()
+        key = hashlib.sha256(b"".join([ex["x"].tobytes(), ex["z"].tobytes(), self.dtype.encode(),
+                                      torch.cuda.get_device_name().encode()])).hexdigest()
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            try:
+                cache = json.load(open(cache_path))
+            except Exception:
+                cache = {}
+        if key in cache:
+            c = cache[key]
+            self.replan(int(c["budget"]), float(c["ratio"]))
+            return dict(c, cached=True)
+        psi = self.empty()
+        psi.normal_()
+        out = self.empty()
+        trials = []
+        for r in ratios:
+            for bmb in budgets_mb:
+                budget = int(bmb * (1 << 20))
+                npass = self.replan(budget, r)
+                self.apply_H(psi, block, out=out)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    self.apply_H(psi, block, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                trials.append({"budget": budget, "ratio": r, "passes": npass, "ms": e0.elapsed_time(e1) / reps})
+        best = min(trials, key=lambda t: t["ms"])
+        self.replan(best["budget"], best["ratio"])
+        res = dict(best, trials=trials, cached=False)
+        if cache_path:
+            cache[key] = {k: best[k] for k in ("budget", "ratio", "passes", "ms")}
+            os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+            json.dump(cache, open(cache_path, "w"), indent=1)
+        return res
+
     def replan(self, l2_budget_bytes: int = 2 << 20, straggler_ratio: float = 1.5):
         """Regroup the matvec passes (L2 budget in bytes, straggler cost ratio)."""
         L.check(self._lib.syk_terms_replan(self._h, int(l2_budget_bytes), float(straggler_ratio)))

@@ -107,6 +107,20 @@ def test_apply_H_multipass_plans_N32(syk, dtype):
         assert h.device_error() == 0
 
 
+def test_autotune_keeps_results_and_caches(syk, tmp_path):
+    N = 36
+    q, J, _ = si.sample_sparse_syk(N, 4, r=13)
+    psi = to_dev(rand_vec(1 << 17, 3), "c64")
+    with syk.Terms(N, q, J, dtype="c64") as h:
+        ref = h.apply_H(psi, 0).clone()
+        rep = h.autotune(budgets_mb=(0.25, 1.0), ratios=(0.0, 1.5), reps=1, cache_path=str(tmp_path / "tune.json"))
+        assert len(rep["trials"]) == 4 and not rep["cached"]
+        got = h.apply_H(psi, 0)
+        assert (torch().max(torch().abs(got - ref)) / torch().max(torch().abs(ref))).item() < 1e-5
+        again = h.autotune(cache_path=str(tmp_path / "tune.json"))
+        assert again["cached"] and again["budget"] == rep["budget"]
+
+
 def test_krylov_multipass_N32(syk):
     """Fused Lanczos epilogues on the last pass of a multi-pass matvec."""
     N = 32
