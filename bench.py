@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="all", choices=["all", "otoc-batch", "otoc-serve"],
+                    help="all: the benchmark line; otoc-batch / otoc-serve: only that leg, as its own JSON line")
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--k", type=float, default=4.0)
     ap.add_argument("--no-fp64", action="store_true")
@@ -172,8 +174,10 @@ def measured_traffic(T, D):
 
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "matvec_c64_traffic.json")))
-        src = open(os.path.join(ROOT, "paper_2311_00639_b300", "csrc", "apply.cu"), "rb").read()
-        if rec.get("apply_cu_sha256") != hashlib.sha256(src).hexdigest():
+        h = hashlib.sha256()
+        for f in ("apply.cu", "tma_common.cuh", "device_common.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_2311_00639_b300", "csrc", f), "rb").read())
+        if rec.get("kernel_sources_sha256") != h.hexdigest():
             return None
         # scale the captured size to this one by term x amplitude work
         return rec["dram_bytes_per_matvec"] * (T * D) / (rec["terms"] * rec["D"])
@@ -433,8 +437,30 @@ def ours(args):
         dist.destroy_process_group()
 
 
+def otoc_only(args):
+    import torch
+
+    build_lib()
+    import paper_2311_00639_b300 as syk
+    import syk_inputs as si
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if args.mode == "otoc-batch":
+        res = otoc_batched(args, syk, si, torch)
+        line = {"metric": "OTOC realizations/s (batched)", "value": res["realizations_per_s"],
+                "unit": "realizations/s", "higher_is_better": True, "config": res}
+    else:
+        res = otoc_served(args, syk, torch)
+        line = {"metric": "OTOC served p50/p99 latency", "value": res["p50_latency_s"], "unit": "s",
+                "higher_is_better": False, "config": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.impl == "ours" and args.mode != "all":
+        otoc_only(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

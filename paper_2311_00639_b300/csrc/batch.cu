@@ -30,6 +30,7 @@
 
 #include "device_common.cuh"
 #include "kernels.cuh"
+#include "tma_common.cuh"
 #include "tridiag.cuh"
 
 namespace syk {
@@ -47,6 +48,9 @@ struct BSlot {
   const uint32_t* x;
   const uint32_t* zi;  // z | imag << 31
   const void* coef[2];
+  const TermF* rec[2];       // complex64: packed records per block
+  const PassPlan* passes;    // class ranges of the records (all passes, in table order)
+  int n_passes;
   int n_terms;
   uint32_t D;
   uint32_t cx[2], cz[2];         // chi strings: [0] = chi_a, [1] = chi_b
@@ -78,6 +82,7 @@ struct BatchArgs {
   double tol;
   double* partA;  // [total blocks]
   double* partN;  // [total blocks]
+  int* err;       // set when a bounded wait expires
 };
 
 template <typename Real>
@@ -335,6 +340,7 @@ __global__ void __launch_bounds__(kBlk) k_b_matvec(BatchArgs a, int j) {
   const BSlot& s = a.slots[si];
   const KScalars* sc = a.sc + si;
   if (sc->m_eff <= j || j + 1 > static_cast<int>(s.D)) return;
+  if (sizeof(Real) == 4 && s.D >= (1u << kTileBits)) return;  // k_b_matvec_c64 handles it
   using C = typename CT<Real>::T;
   const C* v = basis<Real>(s, j);
   const C* vp = j > 0 ? basis<Real>(s, j - 1) : nullptr;
@@ -367,6 +373,112 @@ __global__ void __launch_bounds__(kBlk) k_b_matvec(BatchArgs a, int j) {
   }
   part = block_sum(part);
   if (threadIdx.x == 0) a.partA[blockIdx.x] = part;
+}
+
+// complex64 slots with D >= 2048: the TMA-staged pair-layout matvec of the
+// single-Hamiltonian path (plain tile order), with the Lanczos epilogue.
+template <int S>
+__global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_matvec_c64(BatchArgs a, int j) {
+  constexpr uint32_t kTileBytes = (1u << kTileBits) * 8u;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ int s_err;
+  const int si = a.blk_slot[blockIdx.x];
+  const int2 rg = a.blk_range[si];
+  const BSlot& s = a.slots[si];
+  if (rg.y <= 0 || !s.live || !s.ev || s.done || s.D < (1u << kTileBits)) return;
+  const KScalars* sc = a.sc + si;
+  if (sc->m_eff <= j) return;
+  const uint32_t tl = blockIdx.x - rg.x;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const float2* v = basis<float>(s, j);
+  const float2* vp = j > 0 ? basis<float>(s, j - 1) : nullptr;
+  float2* w = basis<float>(s, j + 1);
+  const TermF* rec = s.rec[s.ev_block];
+  const int T = s.n_terms;
+  const uint32_t ntiles = s.D >> kTileBits;
+  const uint32_t my_tiles = ntiles > tl ? (ntiles - tl - 1) / rg.y + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(smem_u32(&full_bar[i]), 1);
+      mbar_init(smem_u32(&empty_bar[i]), kConsumerWarps);
+    }
+    s_err = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  double part = 0.0;
+  if (warp == kConsumerWarps) {
+    if (lane == 0 && T > 0) {
+      const uint32_t smem0 = smem_u32(smem_raw);
+      const uint64_t keep = l2_policy_evict_last();
+      uint32_t q = 0, issued = 0;
+      for (uint32_t k = 0; k < my_tiles && !*(volatile int*)&s_err; ++k) {
+        const uint32_t tb = (tl + k * rg.y) << kTileBits;
+        for (int tt = 0; tt < T && !*(volatile int*)&s_err; ++tt, ++q) {
+          const uint32_t stg = q % S;
+          if (q >= S && !mbar_wait_bounded(smem_u32(&empty_bar[stg]), ((q / S) - 1) & 1u, &s_err)) break;
+          const float2* src = v + (tb ^ (__ldg(&rec[tt].x) & ~((1u << kTileBits) - 1u)));
+          const uint32_t bar = smem_u32(&full_bar[stg]);
+          mbar_expect_tx(bar, kTileBytes);
+          bulk_g2s_hint(smem0 + stg * kTileBytes, src, kTileBytes, bar, keep);
+          issued = q + 1;
+        }
+      }
+      if (s_err) {
+        for (uint32_t qq = issued > S ? issued - S : 0; qq < issued; ++qq) {
+          const uint32_t bar = smem_u32(&full_bar[qq % S]);
+          const uint64_t ts = globaltimer_ns();
+          while (!mbar_try_wait(bar, (qq / S) & 1u) && globaltimer_ns() - ts < kWaitLimitNs) {
+          }
+        }
+      }
+    }
+  } else {
+    const float bprev = j > 0 ? static_cast<float>(sc->beta[j - 1]) : 0.f;
+    const uint32_t pair_part = warp * 256u + 2u * lane;
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    const float4* vp4 = reinterpret_cast<const float4*>(vp);
+    float4* w4 = reinterpret_cast<float4*>(w);
+    uint64_t q = 0;
+    for (uint32_t k = 0; k < my_tiles; ++k) {
+      const uint32_t mt = ((tl + k * rg.y) << kTileBits) + pair_part;
+      float acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
+      for (int pz = 0; pz < s.n_passes; ++pz) {
+        const int* cl = s.passes[pz].cls;
+        c64_consume<false, false, false, S>(cl[0], cl[1], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<false, false, true, S>(cl[1], cl[2], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<false, true, false, S>(cl[2], cl[3], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<false, true, true, S>(cl[3], cl[4], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<true, false, false, S>(cl[4], cl[5], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<true, false, true, S>(cl[5], cl[6], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<true, true, false, S>(cl[6], cl[7], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<true, true, true, S>(cl[7], cl[8], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t i4 = (mt >> 1) + 32u * r;
+        float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j > 0) pv = vp4[i4];
+        float4 o;
+        o.x = fma_(-bprev, pv.x, acc[r][0]);
+        o.y = fma_(-bprev, pv.y, acc[r][1]);
+        o.z = fma_(-bprev, pv.z, acc[r][2]);
+        o.w = fma_(-bprev, pv.w, acc[r][3]);
+        w4[i4] = o;
+        const float4 vv = v4[i4];
+        part += static_cast<double>(vv.x * o.x + vv.y * o.y) + static_cast<double>(vv.z * o.z + vv.w * o.w);
+      }
+    }
+  }
+  part = block_sum(part);
+  if (threadIdx.x == 0) {
+    a.partA[blockIdx.x] = part;
+    if (s_err) atomicExch(a.err, 1);
+  }
 }
 
 template <typename Real>
@@ -482,6 +594,7 @@ struct Batch {
   int* d_blk_slot = nullptr;
   int2* d_blk_range = nullptr;
   double* d_part = nullptr;  // 2 x max blocks
+  int* d_err = nullptr;      // bounded-wait failure flag
   size_t max_blocks = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -493,7 +606,7 @@ struct Batch {
     if (graph) cudaGraphExecDestroy(graph);
     if (stream) cudaStreamDestroy(stream);
     for (void* p : {static_cast<void*>(d_slots), static_cast<void*>(d_sc), static_cast<void*>(d_blk_slot),
-                    static_cast<void*>(d_blk_range), static_cast<void*>(d_part), arena})
+                    static_cast<void*>(d_blk_range), static_cast<void*>(d_part), static_cast<void*>(d_err), arena})
       if (p) cudaFree(p);
   }
 
@@ -541,11 +654,16 @@ void capture_tick(Batch& b) {
   a.tol = b.tol;
   a.partA = b.d_part;
   a.partN = b.d_part + b.max_blocks;
+  a.err = b.d_err;
   const double brk = sizeof(Real) == 4 ? 1e-7 : 1e-14;
   if (b.graph) {
     cudaGraphExecDestroy(b.graph);
     b.graph = nullptr;
   }
+  constexpr size_t dyn = static_cast<size_t>(kStagesC64) * (1u << kTileBits) * 8u;
+  if (sizeof(Real) == 4)
+    SYK_CUDA(cudaFuncSetAttribute(k_b_matvec_c64<kStagesC64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(dyn)));
   SYK_CUDA(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
   const int S = b.max_slots, G = std::max(1, b.total_blocks);
   k_b_control<Real><<<S, kBlk, 0, b.stream>>>(a);
@@ -553,6 +671,7 @@ void capture_tick(Batch& b) {
   k_b_scale_first<Real><<<G, kBlk, 0, b.stream>>>(a);
   for (int j = 0; j < b.m; ++j) {
     k_b_matvec<Real><<<G, kBlk, 0, b.stream>>>(a, j);
+    if (sizeof(Real) == 4) k_b_matvec_c64<kStagesC64><<<G, 32 * (kConsumerWarps + 1), dyn, b.stream>>>(a, j);
     k_b_axpy_norm<Real><<<G, kBlk, 0, b.stream>>>(a, j);
     k_b_scale_next<Real><<<G, kBlk, 0, b.stream>>>(a, j, brk);
   }
@@ -594,7 +713,9 @@ void relayout(syk::Batch& b) {
   for (int s = 0; s < b.max_slots; ++s) {
     if (!b.jobs[s].live) continue;
     const int64_t D = b.jobs[s].job.h->D;
-    const int nb = static_cast<int>(std::min<int64_t>((D + syk::kBlk - 1) / syk::kBlk, syk::kMaxBlkPerSlot));
+    const bool tiles = b.dtype == SYK_C64 && D >= (int64_t(1) << syk::kTileBits);
+    const int nb = static_cast<int>(tiles ? std::min<int64_t>(D >> syk::kTileBits, syk::kMaxBlkPerSlot)
+                                          : std::min<int64_t>((D + syk::kBlk - 1) / syk::kBlk, syk::kMaxBlkPerSlot));
     range[s] = make_int2(static_cast<int>(blk_slot.size()), nb);
     for (int i = 0; i < nb; ++i) blk_slot.push_back(s);
   }
@@ -641,6 +762,8 @@ int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylo
     SYK_CUDA(cudaMalloc(&b.d_blk_range, max_slots * sizeof(int2)));
     SYK_CUDA(cudaMemset(b.d_blk_range, 0, max_slots * sizeof(int2)));
     SYK_CUDA(cudaMalloc(&b.d_part, 2 * b.max_blocks * sizeof(double)));
+    SYK_CUDA(cudaMalloc(&b.d_err, sizeof(int)));
+    SYK_CUDA(cudaMemset(b.d_err, 0, sizeof(int)));
     SYK_CUDA(cudaMemset(b.d_slots, 0, max_slots * sizeof(syk::BSlot)));
     SYK_CUDA(cudaMemset(b.d_sc, 0, max_slots * sizeof(syk::KScalars)));
     SYK_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
@@ -695,6 +818,10 @@ int syk_batch_submit(syk_batch_t* h, const syk_otoc_job* job) {
     s.zi = t->d_zi;
     s.coef[0] = t->d_coef[0];
     s.coef[1] = t->d_coef[1];
+    s.rec[0] = t->d_termf[0];
+    s.rec[1] = t->d_termf[1];
+    s.passes = t->d_passes;
+    s.n_passes = static_cast<int>(t->passes.size());
     s.n_terms = static_cast<int>(t->terms.size());
     s.D = static_cast<uint32_t>(t->D);
     const syk::ChiString* ch[2] = {&t->chi[job->a], &t->chi[job->b]};
@@ -759,6 +886,9 @@ int syk_batch_run(syk_batch_t* h, int max_ticks, int ticks_per_sync, int* n_fini
       SYK_CUDA(cudaMemcpyAsync(dev_slots.data(), b.d_slots, b.max_slots * sizeof(syk::BSlot), cudaMemcpyDeviceToHost,
                                b.stream));
       SYK_CUDA(cudaStreamSynchronize(b.stream));
+      int derr = 0;
+      SYK_CUDA(cudaMemcpy(&derr, b.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (derr) throw syk::Error(SYK_ETIMEOUT, "a bounded device wait expired; batch results are invalid");
       int finished = 0;
       for (int s = 0; s < b.max_slots; ++s)
         if (b.jobs[s].live && dev_slots[s].done) ++finished;

@@ -1,0 +1,164 @@
+// Bulk-copy (TMA) pipeline helpers and the complex64 pair-layout consumer,
+// shared by the single-Hamiltonian matvec (apply.cu) and the batched engine
+// (batch.cu).
+#pragma once
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace syk {
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// try_wait with a suspend-time hint: the thread may sleep in hardware until
+// the phase completes or about `ns` nanoseconds pass, instead of spinning.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// L2 eviction-priority policies (createpolicy) for bulk copies and stores.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
+                                              uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void st_f4_hint(float4* ptr, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
+
+// Bounded wait; returns false (and sets *s_err) on timeout or if another
+// thread already recorded an error.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int* s_err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t_start = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;  // sleep up to 0.1 ms per try
+    if (*s_err) return false;
+    if (globaltimer_ns() - t_start > kWaitLimitNs) {
+      *s_err = 1;
+      return false;
+    }
+  }
+}
+
+constexpr int kConsumerWarps = 8;
+#ifndef SYK_C64_STAGES
+#define SYK_C64_STAGES 4
+#endif
+constexpr int kStagesC64 = SYK_C64_STAGES;
+// CTAs per SM: shared memory holds S 16 KiB stages each (<= 227 KiB per SM);
+// 72 registers x 288 threads allow at most 3.
+constexpr int kC64CtasPerSm = (227 / (16 * kStagesC64 + 2)) < 3 ? (227 / (16 * kStagesC64 + 2)) : 3;
+
+template <bool IMAG, bool XS, bool ZS, int XR>
+__device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t pa2, const float c[4],
+                                         float (&a)[4][4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const float4 v = t4[pa2 + 32u * static_cast<uint32_t>(r ^ XR)];
+    // inputs of amplitude m (even) and m + 1
+    const float i0r = XS ? v.z : v.x, i0i = XS ? v.w : v.y;
+    const float i1r = XS ? v.x : v.z, i1i = XS ? v.y : v.w;
+    const float c0 = c[r];
+    const float c1 = ZS ? -c[r] : c[r];
+    if (!IMAG) {
+      a[r][0] = fma_(c0, i0r, a[r][0]);
+      a[r][1] = fma_(c0, i0i, a[r][1]);
+      a[r][2] = fma_(c1, i1r, a[r][2]);
+      a[r][3] = fma_(c1, i1i, a[r][3]);
+    } else {  // (i c) * v = c * (-v.im, v.re)
+      a[r][0] = fma_(-c0, i0i, a[r][0]);
+      a[r][1] = fma_(c0, i0r, a[r][1]);
+      a[r][2] = fma_(-c1, i1i, a[r][2]);
+      a[r][3] = fma_(c1, i1r, a[r][3]);
+    }
+  }
+}
+
+template <bool IMAG, bool XS, bool ZS, int S>
+__device__ __forceinline__ void c64_consume(int tb0, int tb1, uint64_t& q, float (&a)[4][4],
+                                            const TermF* __restrict__ rec, uint32_t mt, uint32_t pair_part,
+                                            const unsigned char* smem, uint64_t* full_bar, uint64_t* empty_bar,
+                                            volatile int* s_err, uint32_t lane) {
+  for (int tt = tb0; tt < tb1; ++tt, ++q) {
+    const uint32_t stg = static_cast<uint32_t>(q % S);
+    const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), static_cast<uint32_t>((q / S) & 1), s_err);
+    if (ok) {
+      const uint4 d = __ldg(reinterpret_cast<const uint4*>(rec + tt));
+      const uint32_t x = d.x, z = d.y;
+      const float cf = __uint_as_float(d.z);
+      const uint32_t sl = __popc(z & mt) & 1u;
+      const uint32_t zr = (z >> 6) & 3u;
+      const uint32_t s1 = sl ^ (zr & 1u), s2 = sl ^ (zr >> 1);
+      const float c[4] = {sgnflip(cf, sl), sgnflip(cf, s1), sgnflip(cf, s2), sgnflip(cf, s1 ^ (zr >> 1))};
+      const uint32_t pa2 = (pair_part ^ (x & 0x73Eu)) >> 1;  // float4 index of the row-0 input pair
+      const float4* t4 = reinterpret_cast<const float4*>(smem + stg * (1u << kTileBits) * 8u);
+      switch ((x >> 6) & 3u) {
+        case 0: c64_rows<IMAG, XS, ZS, 0>(t4, pa2, c, a); break;
+        case 1: c64_rows<IMAG, XS, ZS, 1>(t4, pa2, c, a); break;
+        case 2: c64_rows<IMAG, XS, ZS, 2>(t4, pa2, c, a); break;
+        default: c64_rows<IMAG, XS, ZS, 3>(t4, pa2, c, a); break;
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && ok) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty_bar[stg])) : "memory");
+  }
+}
+
+}  // namespace
+}  // namespace syk

@@ -109,27 +109,39 @@ __device__ void tridiag_warp(KScalars* sc, int m, double z_re, double z_im, doub
   // Substep search: largest s = 2^-k with estimated local error <= tol * s.
   // Estimates (relative to ||c||): beta_m |e_m^T e^{-hT} e_1| and
   // beta_m |h| |e_m^T phi_1(-hT) e_1| (Saad 1992, Thm. 5.1), the larger one.
+  // Each lane evaluates the exponentials of its own eigenvalues (k = lane,
+  // lane + 32) once per attempt; the small products then use shared memory.
+  __shared__ double Er[kMaxKrylov], Ei[kMaxKrylov], Pr[kMaxKrylov], Pi[kMaxKrylov];
   double s_frac = 1.0, err = 0.0;
   bool ok = false;
   for (int attempt = 0; attempt < 64 && status == 0; ++attempt) {
     const double hr = s_frac * z_re, hi = s_frac * z_im;
+    for (int k = lane; k < n; k += 32) {
+      const double w0 = Z[0][k];
+      const double2 ex = cexp_(-hr * d[k], -hi * d[k]);
+      const double2 ph = phi1_(-hr * d[k], -hi * d[k]);
+      Er[k] = ex.x * w0;
+      Ei[k] = ex.y * w0;
+      Pr[k] = ph.x * w0;
+      Pi[k] = ph.y * w0;
+    }
+    __syncwarp();
     double cr0 = 0, ci0 = 0, cr1 = 0, ci1 = 0;  // rows lane, lane+32
     double pr_last = 0, pi_last = 0;
     for (int k = 0; k < n; ++k) {
-      const double2 ex = cexp_(-hr * d[k], -hi * d[k]);
-      const double w0 = Z[0][k];
+      const double er = Er[k], ei = Ei[k];
       if (lane < n) {
-        cr0 += Z[lane][k] * ex.x * w0;
-        ci0 += Z[lane][k] * ex.y * w0;
+        cr0 += Z[lane][k] * er;
+        ci0 += Z[lane][k] * ei;
       }
       if (lane + 32 < n) {
-        cr1 += Z[lane + 32][k] * ex.x * w0;
-        ci1 += Z[lane + 32][k] * ex.y * w0;
+        cr1 += Z[lane + 32][k] * er;
+        ci1 += Z[lane + 32][k] * ei;
       }
-      const double2 ph = phi1_(-hr * d[k], -hi * d[k]);
-      pr_last += Z[n - 1][k] * ph.x * w0;
-      pi_last += Z[n - 1][k] * ph.y * w0;
+      pr_last += Z[n - 1][k] * Pr[k];
+      pi_last += Z[n - 1][k] * Pi[k];
     }
+    __syncwarp();
     const double nc = sqrt(warp_sum_(cr0 * cr0 + ci0 * ci0 + cr1 * cr1 + ci1 * ci1));
     // |c_{n-1}|: owned by lane (n-1) % 32 in slot (n-1) / 32.
     const int owner = (n - 1) & 31;
