@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="all", choices=["all", "otoc-batch", "otoc-serve"],
+    ap.add_argument("--mode", default="all", choices=["all", "otoc-batch", "otoc-serve", "n64-otoc"],
                     help="all: the benchmark line; otoc-batch / otoc-serve: only that leg, as its own JSON line")
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--k", type=float, default=4.0)
@@ -445,6 +445,24 @@ def otoc_only(args):
     import syk_inputs as si
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if args.mode == "n64-otoc":
+        # End-to-end OTOC at N=64: complex64 states, FP64 scalars, two-pass Lanczos (m=20),
+        # beta=10, one Philox state, t in {0, 0.5}; both parity blocks.
+        q, J, _ = si.sample_sparse_syk(args.N, args.k, r=0)
+        h = syk.Terms(args.N, q, J, dtype="c64")
+        grid = [0.0, 0.5]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F, o, st = h.otoc(args.N - 1, args.N - 2, 10.0, grid, n_states=1, seed=2024, m=20, two_pass=True)
+        wall = time.perf_counter() - t0
+        line = {"metric": "end-to-end OTOC time per t-point at N=64 (c64 states, FP64 scalars)",
+                "value": wall / len(grid), "unit": "s/point", "higher_is_better": False,
+                "config": {"workload": f"N={args.N}, k={args.k:g}, T={h.n_terms}, beta=10, 1 state, t={grid}, "
+                                       "Lanczos m=20 two-pass", "wall_s": wall, "matvecs": st.matvecs,
+                           "substeps": st.substeps, "F": [[z.real, z.imag] for z in F[0]], "otoc": list(o),
+                           "s_per_matvec": wall / max(1, st.matvecs)}}
+        print(json.dumps(line), flush=True)
+        return
     if args.mode == "otoc-batch":
         res = otoc_batched(args, syk, si, torch)
         line = {"metric": "OTOC realizations/s (batched)", "value": res["realizations_per_s"],

@@ -267,7 +267,10 @@ typedef struct {
   int* status_out;           /* HOST, optional: SYK_OK or SYK_ENOCONV when the job finishes */
   int64_t basis_index;       /* < 0: typical state; else the basis state g = block*D + m of the
                                 full space (exact trace = sum of these jobs over g, divided by 2D) */
+  int kind;                  /* SYK_JOB_OTOC, or SYK_JOB_GREEN: G(t) = <psi| e^{(it-b/2)H} chi_a
+                                e^{-iHt} chi_a e^{-bH/2} |psi> (supplement, Green function; b unused) */
 } syk_otoc_job;
+enum { SYK_JOB_OTOC = 0, SYK_JOB_GREEN = 1 };
 /* max_bytes: device arena for job state (allocated once); max_slots: jobs in flight. */
 int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylov_params* p, syk_batch_t** out);
 int syk_batch_destroy(syk_batch_t* batch);

@@ -136,3 +136,39 @@ def normalise(F) -> np.ndarray:
     """OTOC(t) = Re F(t) / Re F(0) (F(0) = F[0])."""
     F = np.asarray(F)
     return F.real / F.real[0]
+
+
+# --- Green function (supplement, G(t) paragraph) ----------------------------
+#   G(t) = <psi| e^{(it - b/2)H} chi_a e^{-iHt} chi_a e^{-bH/2} |psi>,
+#   G_R(t) = Re G(t) / Re G(0); the paper uses a = N-1.
+#   In parity blocks G = sum_P <psi_P| e^{(it-b/2)H_PP} chi_a^{PQ}
+#   e^{-iH_QQ t} chi_a^{QP} e^{-bH_PP/2} |psi_P>.
+def G_state(H, X, a: int, beta: float, ts, psi, eigpair=None) -> np.ndarray:
+    lam, V = dyn.eig(H) if eigpair is None else eigpair
+    Xa = V.conj().T @ X[a] @ V
+    p = V.conj().T @ np.asarray(psi, dtype=np.complex128)
+    out = []
+    for t in np.asarray(ts, dtype=np.float64):
+        k = np.exp(-beta / 2.0 * lam) * p
+        k = Xa @ (np.exp(-1j * t * lam) * (Xa @ k))
+        bra = np.exp(-(1j * t + beta / 2.0) * lam) * p  # e^{-(it+b/2)H} psi
+        out.append(np.vdot(bra, k))
+    return np.array(out)
+
+
+def G_state_blocks(N, rep, HUU, HDD, X, a, beta, ts, psi_U, psi_D) -> np.ndarray:
+    Hs = (HUU, HDD)
+    eigs = (dyn.eig(HUU), dyn.eig(HDD))
+    psis = (np.asarray(psi_U, np.complex128), np.asarray(psi_D, np.complex128))
+    out = np.zeros(len(ts), dtype=np.complex128)
+    for P in (0, 1):
+        Q = 1 - P
+        ev = lambda blk, z, v: dyn.evolve(Hs[blk], z, v, eigs[blk])
+        u0 = ev(P, beta / 2.0, psis[P])
+        for n, t in enumerate(np.asarray(ts, dtype=np.float64)):
+            k = ham.block_of(X[a], N, rep, Q, P) @ u0
+            k = ev(Q, 1j * t, k)
+            k = ham.block_of(X[a], N, rep, P, Q) @ k
+            bra = ev(P, 1j * t + beta / 2.0, psis[P])
+            out[n] += np.vdot(bra, k)
+    return out

@@ -33,7 +33,7 @@ class OtocJob(C.Structure):
     _fields_ = [("h", C.c_void_p), ("a", C.c_int), ("b", C.c_int), ("beta", C.c_double), ("t_grid", C.c_void_p),
                 ("n_t", C.c_int), ("seed", C.c_uint64), ("state_id", C.c_uint64), ("tag", C.c_int64),
                 ("F_out", C.c_void_p), ("stats", C.c_void_p), ("status_out", C.c_void_p),
-                ("basis_index", C.c_int64)]
+                ("basis_index", C.c_int64), ("kind", C.c_int)]
 
 
 # name -> (restype, argtypes); every symbol include/syk.h declares.

@@ -323,7 +323,8 @@ class Batch:
         return int(self._lib.syk_batch_job_bytes(self._h, terms._h, int(n_t)))
 
     def submit(self, terms: "Terms", a: int, b: int, beta: float, t_grid, seed: int, state_id: int, tag: int,
-               basis_index: int = -1) -> bool:
+               basis_index: int = -1, kind: str = "otoc") -> bool:
+        """kind: "otoc" (Eq. (2), F(t)) or "green" (G(t) with Majorana a; b unused)."""
         if terms.dtype != self.dtype:
             raise ValueError("terms dtype differs from the batch dtype")
         tg = np.ascontiguousarray(np.asarray(t_grid, dtype=np.float64))
@@ -332,7 +333,7 @@ class Batch:
         status = C.c_int(0)
         job = L.OtocJob(terms._h, int(a), int(b), float(beta), tg.ctypes.data, len(tg), C.c_uint64(seed),
                         C.c_uint64(state_id), int(tag), F.ctypes.data, C.addressof(st), C.addressof(status),
-                        int(basis_index))
+                        int(basis_index), 1 if kind == "green" else 0)
         rc = self._lib.syk_batch_submit(self._h, C.byref(job))
         if rc == L.SYK_EAGAIN:
             return False

@@ -40,7 +40,7 @@ namespace {
 constexpr int kBlk = 256;          // threads per block
 constexpr int kMaxBlkPerSlot = 256;  // blocks per slot (partials summed per slot)
 
-enum Stage { S_INIT = 0, S_PART, S_AFTER_U0, S_POINT, S_K1, S_K2, S_K3, S_K4, S_DONE };
+enum Stage { S_INIT = 0, S_PART, S_AFTER_U0, S_POINT, S_K1, S_K2, S_K3, S_K4, S_G1, S_G2, S_DONE };
 
 // Device-resident slot descriptor.
 struct BSlot {
@@ -62,6 +62,7 @@ struct BSlot {
   double* F;         // device [n_t][2]
   uint64_t seed, state_id;
   long long basis;  // < 0: Philox typical state; else basis state index g = block*D + m
+  int kind;         // SYK_JOB_OTOC or SYK_JOB_GREEN
   void* vec[4];  // u0, bra, k1, k2
   void* V;       // basis, (m+1) x D
   // state machine
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(kBlk) k_b_control(BatchArgs a) {
         o.y = static_cast<Real>(v.y * inv);
         u0[m] = o;
       }
-      start_evolve(0, P, s.beta / 8.0, 0.0, S_AFTER_U0);
+      start_evolve(0, P, s.kind == SYK_JOB_GREEN ? s.beta / 2.0 : s.beta / 8.0, 0.0, S_AFTER_U0);
     } else if (stage == S_AFTER_U0) {
       const C* u0 = cvec<Real>(s, 0);
       C* bra = mvec<Real>(s, 1);
@@ -244,8 +245,30 @@ __global__ void __launch_bounds__(kBlk) k_b_control(BatchArgs a) {
         const double dt = t - s.tprev;
         __syncthreads();
         if (threadIdx.x == 0) s.tprev = t;
-        start_evolve(1, P, 0.0, dt, S_K1);
+        start_evolve(1, P, 0.0, dt, s.kind == SYK_JOB_GREEN ? S_G1 : S_K1);
       }
+    } else if (stage == S_G1) {
+      blk_chi<Real>(s, 0, P, cvec<Real>(s, 0), mvec<Real>(s, 2));  // k1 = chi_a u0
+      start_evolve(2, Q, 0.0, s.tg[s.n], S_G2);
+    } else if (stage == S_G2) {
+      blk_chi<Real>(s, 0, Q, cvec<Real>(s, 2), mvec<Real>(s, 3));  // k2 = chi_a k1
+      const C* bra = cvec<Real>(s, 1);
+      const C* ket = cvec<Real>(s, 3);
+      double sr = 0.0, si = 0.0;
+      for (uint32_t m = threadIdx.x; m < s.D; m += blockDim.x) {
+        const C u = bra[m], v = ket[m];
+        sr += static_cast<double>(u.x) * v.x + static_cast<double>(u.y) * v.y;
+        si += static_cast<double>(u.x) * v.y - static_cast<double>(u.y) * v.x;
+      }
+      sr = block_sum(sr);
+      si = block_sum(si);
+      if (threadIdx.x == 0) {
+        s.F[2 * s.n] += sr;
+        s.F[2 * s.n + 1] += si;
+        s.n += 1;
+        s.stage = S_POINT;
+      }
+      __syncthreads();
     } else if (stage == S_K1) {
       blk_chi<Real>(s, 1, P, cvec<Real>(s, 0), mvec<Real>(s, 2));  // k1 = chi_b u0
       start_evolve(2, Q, s.beta / 4.0, s.tg[s.n], S_K2);
@@ -839,6 +862,8 @@ int syk_batch_submit(syk_batch_t* h, const syk_otoc_job* job) {
     s.state_id = job->state_id;
     SYK_REQUIRE(job->basis_index < 2 * t->D, "basis_index out of range [0, 2D)");
     s.basis = job->basis_index < 0 ? -1 : job->basis_index;
+    SYK_REQUIRE(job->kind == SYK_JOB_OTOC || job->kind == SYK_JOB_GREEN, "bad job kind");
+    s.kind = job->kind;
     for (int i = 0; i < 4; ++i) s.vec[i] = base + i * vb;
     s.V = base + 4 * vb;
     char* tail = base + (4 + b.m + 1) * vb;

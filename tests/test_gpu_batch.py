@@ -119,3 +119,23 @@ def test_batch_arena_refuses_beyond_budget(syk):
         assert b.info()["bytes_in_use"] == admitted * need
         res = b.drain()
         assert len(res) == admitted and b.info()["bytes_in_use"] == 0
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_batch_green_function_matches_oracle(syk, dtype):
+    """G(t) of the supplement (Green function paragraph) as a batch job kind."""
+    N = 12
+    rep = "jw"
+    q, J, _ = si.sample_sparse_syk(N, 4, r=31)
+    HU, HD = ham.blocks(ham.dense_H(N, q, J, rep), N, rep)
+    X = mj.chis(N, rep)
+    ts = np.array([0.0, 0.4, 1.3, 3.0])
+    tol = 1e-10 if dtype == "c128" else 2e-4
+    with syk.Terms(N, q, J, dtype=dtype) as h, syk.Batch(dtype=dtype, max_slots=4, max_bytes=64 << 20) as b:
+        for tag, (a, beta) in enumerate([(N - 1, 5.0), (3, 0.0)]):
+            assert b.submit(h, a, 0, beta, ts, 17, tag, tag, kind="green")
+        res = {r["tag"]: r for r in b.drain()}
+        for tag, (a, beta) in enumerate([(N - 1, 5.0), (3, 0.0)]):
+            pU, pD = philox_normed(N, 17, tag)
+            ref = ot.G_state_blocks(N, rep, HU, HD, X, a, beta, ts, pU, pD)
+            assert np.max(np.abs(res[tag]["F"] - ref)) < tol

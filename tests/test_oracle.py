@@ -326,3 +326,43 @@ def test_coupling_law():
         assert np.all(q[:, 0] < q[:, 1]) and np.all(q[:, 2] < q[:, 3]) and np.all(q[:, 1] < q[:, 2])
     assert abs(np.mean(Ts) - k * N) < 4 * math.sqrt(k * N / 20)
     assert abs(np.mean(vs) - 1.0) < 0.1
+
+
+# --- Green function (supplement, G(t) paragraph) closed forms
+@pytest.mark.parametrize("rep", REPS)
+def test_green_closed_forms(rep):
+    N, a = 10, 9
+    X = mj.chis(N, rep)
+    rng = np.random.default_rng(8)
+    ts = [0.0, 0.6, 2.2]
+    # no term contains chi_a: chi_a commutes with H, G(t) = <psi|e^{-bH}|psi>/2 for all t
+    q, J = _commuting_instance(N, a, 8, 5, False)
+    H = ham.dense_H(N, q, J, rep)
+    psi = _normed(rng.normal(size=H.shape[0]) + 1j * rng.normal(size=H.shape[0]))
+    for beta in (0.0, 4.0):
+        ref = 0.5 * np.vdot(psi, sla.expm(-beta * H) @ psi)
+        assert np.allclose(otoc.G_state(H, X, a, beta, ts, psi), ref, atol=1e-12)
+    # every term contains chi_a: chi_a e^{-iHt} chi_a = e^{iHt}/2, G(t) = <psi|e^{(2it-b)H}|psi>/2
+    q, J = _commuting_instance(N, a, 8, 4, True)
+    H = ham.dense_H(N, q, J, rep)
+    for beta in (0.0, 3.0):
+        ref = [0.5 * np.vdot(psi, sla.expm((2j * t - beta) * H) @ psi) for t in ts]
+        assert np.allclose(otoc.G_state(H, X, a, beta, ts, psi), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("rep", REPS)
+def test_green_block_form_equals_full_space(rep):
+    N = 10
+    q, J = _instance(N, r=9)
+    H = ham.dense_H(N, q, J, rep)
+    HU, HD = ham.blocks(H, N, rep)
+    X = mj.chis(N, rep)
+    pU, pD = si.random_state(N, seed=3)
+    ts = np.array([0.0, 0.7, 2.5])
+    for beta in (0.0, 5.0):
+        full = otoc.G_state(H, X, N - 1, beta, ts, mj.to_full(pU, pD, N, rep))
+        blk = otoc.G_state_blocks(N, rep, HU, HD, X, N - 1, beta, ts, pU, pD)
+        assert np.allclose(full, blk, atol=1e-13)
+        # G(0) = <psi|e^{-bH}|psi>/2 for any H (chi_a^2 = 1/2)
+        psi = mj.to_full(pU, pD, N, rep)
+        assert np.isclose(full[0], 0.5 * np.vdot(psi, sla.expm(-beta * H) @ psi), atol=1e-13)
