@@ -416,28 +416,28 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
       cy.x = static_cast<float>(p.sc->beta0 * p.sc->c_re[p.j + 1]);
       cy.y = static_cast<float>(p.sc->beta0 * p.sc->c_im[p.j + 1]);
     }
-    const uint32_t pair_part = warp * 256u + 2u * lane;
+    const uint32_t pair_part = warp * (64u * kRows) + 2u * lane;
     const uint64_t out_pol = l2_policy_evict_first();  // output tiles are not re-read within the pass
     const float4* psi4 = reinterpret_cast<const float4*>(psi);
     float4* out4 = reinterpret_cast<float4*>(out);
     uint64_t q = 0;
     for (uint32_t k = 0; k < my_tiles; ++k) {
       const uint32_t mt = tile_base(k) + pair_part;  // amplitude of row 0, even
-      float4 prev[4];
+      float4 prev[kRows];
       if (ACCUM) {  // the producer's first job of the tile is this tile of `out`
         const uint32_t stg = static_cast<uint32_t>(q % S);
         const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), static_cast<uint32_t>((q / S) & 1), &s_err);
         const float4* t4 = reinterpret_cast<const float4*>(smem_raw + stg * kTileBytes);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) prev[r] = ok ? t4[(pair_part >> 1) + 32u * r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int r = 0; r < kRows; ++r) prev[r] = ok ? t4[(pair_part >> 1) + 32u * r] : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncwarp();
         if (lane == 0 && ok)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty_bar[stg])) : "memory");
         ++q;
       }
-      float a[4][4];
+      float a[kRows][4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
+      for (int r = 0; r < kRows; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
       c64_consume<false, false, false, S>(cls[0], cls[1], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
       c64_consume<false, false, true, S>(cls[1], cls[2], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
       c64_consume<false, true, false, S>(cls[2], cls[3], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
       c64_consume<true, true, false, S>(cls[6], cls[7], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
       c64_consume<true, true, true, S>(cls[7], cls[8], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < kRows; ++r) {
         const uint32_t i4 = (mt >> 1) + 32u * r;
         if (ACCUM) {
           a[r][0] += prev[r].x;

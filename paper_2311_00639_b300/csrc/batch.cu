@@ -460,16 +460,16 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
     }
   } else {
     const float bprev = j > 0 ? static_cast<float>(sc->beta[j - 1]) : 0.f;
-    const uint32_t pair_part = warp * 256u + 2u * lane;
+    const uint32_t pair_part = warp * (64u * kRows) + 2u * lane;
     const float4* v4 = reinterpret_cast<const float4*>(v);
     const float4* vp4 = reinterpret_cast<const float4*>(vp);
     float4* w4 = reinterpret_cast<float4*>(w);
     uint64_t q = 0;
     for (uint32_t k = 0; k < my_tiles; ++k) {
       const uint32_t mt = ((tl + k * rg.y) << kTileBits) + pair_part;
-      float acc[4][4];
+      float acc[kRows][4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
+      for (int r = 0; r < kRows; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
       for (int pz = 0; pz < s.n_passes; ++pz) {
         const int* cl = s.passes[pz].cls;
         c64_consume<false, false, false, S>(cl[0], cl[1], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
         c64_consume<true, true, true, S>(cl[7], cl[8], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < kRows; ++r) {
         const uint32_t i4 = (mt >> 1) + 32u * r;
         float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (j > 0) pv = vp4[i4];

@@ -96,20 +96,28 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   }
 }
 
-constexpr int kConsumerWarps = 8;
+// Consumer layout: each lane owns two neighbouring amplitudes in kRows rows of
+// 64 amplitudes (m = tile + warp*64*kRows + 64 r + 2 lane + {0,1}); the warps of
+// a CTA tile the 2048-amplitude tile.
+#ifndef SYK_C64_ROWS
+#define SYK_C64_ROWS 8
+#endif
+constexpr int kRows = SYK_C64_ROWS;
+constexpr int kConsumerWarps = (1 << kTileBits) / (64 * kRows);
+constexpr uint32_t kRowMask = static_cast<uint32_t>(kRows - 1) << 6;  // amplitude bits chosen by the row
+constexpr uint32_t kPairXMask = 0x7FEu & ~kRowMask;                    // in-tile flip bits applied per lane
 #ifndef SYK_C64_STAGES
 #define SYK_C64_STAGES 4
 #endif
 constexpr int kStagesC64 = SYK_C64_STAGES;
-// CTAs per SM: shared memory holds S 16 KiB stages each (<= 227 KiB per SM);
-// 72 registers x 288 threads allow at most 3.
+// CTAs per SM: shared memory holds S 16 KiB stages each (<= 227 KiB per SM), at most 3.
 constexpr int kC64CtasPerSm = (227 / (16 * kStagesC64 + 2)) < 3 ? (227 / (16 * kStagesC64 + 2)) : 3;
 
 template <bool IMAG, bool XS, bool ZS, int XR>
-__device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t pa2, const float c[4],
-                                         float (&a)[4][4]) {
+__device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t pa2, const float (&c)[kRows],
+                                         float (&a)[kRows][4]) {
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < kRows; ++r) {
     const float4 v = t4[pa2 + 32u * static_cast<uint32_t>(r ^ XR)];
     // inputs of amplitude m (even) and m + 1
     const float i0r = XS ? v.z : v.x, i0i = XS ? v.w : v.y;
@@ -131,7 +139,7 @@ __device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t
 }
 
 template <bool IMAG, bool XS, bool ZS, int S>
-__device__ __forceinline__ void c64_consume(int tb0, int tb1, uint64_t& q, float (&a)[4][4],
+__device__ __forceinline__ void c64_consume(int tb0, int tb1, uint64_t& q, float (&a)[kRows][4],
                                             const TermF* __restrict__ rec, uint32_t mt, uint32_t pair_part,
                                             const unsigned char* smem, uint64_t* full_bar, uint64_t* empty_bar,
                                             volatile int* s_err, uint32_t lane) {
@@ -141,18 +149,27 @@ __device__ __forceinline__ void c64_consume(int tb0, int tb1, uint64_t& q, float
     if (ok) {
       const uint4 d = __ldg(reinterpret_cast<const uint4*>(rec + tt));
       const uint32_t x = d.x, z = d.y;
-      const float cf = __uint_as_float(d.z);
-      const uint32_t sl = __popc(z & mt) & 1u;
-      const uint32_t zr = (z >> 6) & 3u;
-      const uint32_t s1 = sl ^ (zr & 1u), s2 = sl ^ (zr >> 1);
-      const float c[4] = {sgnflip(cf, sl), sgnflip(cf, s1), sgnflip(cf, s2), sgnflip(cf, s1 ^ (zr >> 1))};
-      const uint32_t pa2 = (pair_part ^ (x & 0x73Eu)) >> 1;  // float4 index of the row-0 input pair
+      const uint32_t cb = d.z;
+      // sign (-1)^{popc(z & m)} of row r: the lane/warp/tile part popc(z & mt)
+      // and the row part popc(z & 64 r) = parity of (z >> 6) & r, folded into
+      // the coefficient's sign bit.
+      const uint32_t s0 = (__popc(z & mt) << 31) ^ cb;
+      const uint32_t p0 = (z << 25) & 0x80000000u, p1 = (z << 24) & 0x80000000u, p2 = (z << 23) & 0x80000000u;
+      float c[kRows];
+#pragma unroll
+      for (int r = 0; r < kRows; ++r)
+        c[r] = __uint_as_float(s0 ^ ((r & 1) ? p0 : 0u) ^ ((r & 2) ? p1 : 0u) ^ ((r & 4) ? p2 : 0u));
+      const uint32_t pa2 = (pair_part ^ (x & kPairXMask)) >> 1;  // float4 index of the row-0 input pair
       const float4* t4 = reinterpret_cast<const float4*>(smem + stg * (1u << kTileBits) * 8u);
-      switch ((x >> 6) & 3u) {
+      switch ((x & kRowMask) >> 6) {
         case 0: c64_rows<IMAG, XS, ZS, 0>(t4, pa2, c, a); break;
-        case 1: c64_rows<IMAG, XS, ZS, 1>(t4, pa2, c, a); break;
-        case 2: c64_rows<IMAG, XS, ZS, 2>(t4, pa2, c, a); break;
-        default: c64_rows<IMAG, XS, ZS, 3>(t4, pa2, c, a); break;
+        case 1: c64_rows<IMAG, XS, ZS, 1 % kRows>(t4, pa2, c, a); break;
+        case 2: c64_rows<IMAG, XS, ZS, 2 % kRows>(t4, pa2, c, a); break;
+        case 3: c64_rows<IMAG, XS, ZS, 3 % kRows>(t4, pa2, c, a); break;
+        case 4: c64_rows<IMAG, XS, ZS, 4 % kRows>(t4, pa2, c, a); break;
+        case 5: c64_rows<IMAG, XS, ZS, 5 % kRows>(t4, pa2, c, a); break;
+        case 6: c64_rows<IMAG, XS, ZS, 6 % kRows>(t4, pa2, c, a); break;
+        default: c64_rows<IMAG, XS, ZS, 7 % kRows>(t4, pa2, c, a); break;
       }
     }
     __syncwarp();
