@@ -374,21 +374,23 @@ def ours(args):
         del psi64, out64
         h64.close()
 
-    # the same kernel on an L2-resident block (N=40, 4 MiB, one pass): the
-    # data-movement ceiling of one 8-byte operand per term x amplitude
+    # the same kernel on an L2-resident block (N=46, k=8: 32 MiB per vector,
+    # input + output 64 MiB of the 126 MB L2, one pass, 2048 tiles over 444
+    # CTAs): the data-movement ceiling of one 8-byte operand per term x amplitude
     l2res = None
     if not args.no_l2:
-        q40, J40, _ = si.sample_sparse_syk(40, 16.0, r=rank)
-        h40 = syk.Terms(40, q40, J40, dtype="c64")
-        h40.replan(256 << 20, 0.0)
-        p40, _ = h40.random_state(seed=7, state_id=0, blocks=(0,))
-        o40 = h40.empty()
-        k40 = 200
-        d40 = time_matvecs(h40, p40, o40, k40, 20, torch)
-        rate = h40.n_terms * h40.D * k40 / d40
-        l2res = {"N": 40, "k": 16, "terms": h40.n_terms, "D": h40.D, "value": rate / 1e9, "unit": UNIT,
+        q46, J46, _ = si.sample_sparse_syk(46, 8.0, r=rank)
+        h46 = syk.Terms(46, q46, J46, dtype="c64")
+        h46.replan(256 << 20, 0.0)
+        p46, _ = h46.random_state(seed=7, state_id=0, blocks=(0,))
+        o46 = h46.empty()
+        k46 = 100
+        d46 = time_matvecs(h46, p46, o46, k46, 10, torch)
+        rate = h46.n_terms * h46.D * k46 / d46
+        l2res = {"N": 46, "k": 8, "terms": h46.n_terms, "D": h46.D, "value": rate / 1e9, "unit": UNIT,
                  "operand_GBps": rate * 8 / 1e9}
-        h40.close()
+        h46.close()
+        del p46, o46
 
     # roofline of the matvec kernel
     peaks = {}

@@ -26,6 +26,11 @@
  *     tensors); the library never frees caller memory.  Pointers must be
  *     16-byte aligned.  Every call with a cudaStream_t is asynchronous on that
  *     stream unless stated otherwise.
+ *   * A complex64 handle keeps a device tile counter that its H psi passes
+ *     draw work from; calls that apply one handle (syk_apply_H,
+ *     syk_krylov_evolve[_noalloc], syk_otoc) must therefore not overlap on
+ *     the GPU: issue them on one stream, or order the streams with events.
+ *     Different handles are independent.
  *   * Return value: SYK_OK (0) or a negative status.  syk_last_error() gives
  *     the message of the last failing call on the calling thread.  No C++
  *     exception crosses this interface.
@@ -95,13 +100,16 @@ int syk_terms_get_info(const syk_terms_t* h, syk_terms_info* info);
  * syk_terms_replan — regroup the terms into matvec passes.  Each pass fixes a
  * set of high index bits that its terms do not flip and visits the block one
  * fixed value of those bits at a time ("super-tile"), so that its inputs are
- * re-read from L2; l2_budget_bytes bounds the super-tile size (default 2 MiB,
- * used by syk_build_terms).  straggler_ratio > 0 (default 1.5, the best of a
- * sweep on B300 at N = 64) lets the planner dissolve light passes, moving their
+ * re-read from L2; l2_budget_bytes bounds the super-tile size.
+ * straggler_ratio > 0 lets the planner dissolve light passes, moving their
  * terms into heavier passes that fetch them from HBM instead; 0 disables it.
- * Synchronises the device and re-uploads the table; results are unchanged up
- * to floating-point summation order.  Not to be called while the handle is in
- * use on a stream.
+ * l2_budget_bytes = 0 restores the default plan of syk_build_terms (the best
+ * of a sweep on B300 at N = 64: complex64 32 MiB and ratio 3, complex128
+ * 2 MiB and ratio 1.5; straggler_ratio is then ignored).  Synchronises the
+ * device and re-uploads the table; results are unchanged up to floating-point
+ * summation order.  Not to be called while the handle is in use on a stream.
+ * Errors: SYK_EINVAL (l2_budget_bytes in 1..4095, negative or non-finite
+ * straggler_ratio).
  */
 int syk_terms_replan(syk_terms_t* h, size_t l2_budget_bytes, double straggler_ratio);
 /*

@@ -136,7 +136,7 @@ class Terms:
         L.check(self._lib.syk_terms_get_info(self._h, C.byref(info)))
         return int(info.device_error)
 
-    def autotune(self, budgets_mb=(0.5, 1.0, 2.0, 4.0, 8.0), ratios=(0.0, 1.5, 3.0), reps: int = 2, block: int = 0,
+    def autotune(self, budgets_mb=(2.0, 8.0, 32.0, 64.0), ratios=(0.0, 1.5, 3.0), reps: int = 2, block: int = 0,
                  cache_path=None) -> dict:
         """Pick the matvec pass plan (L2 budget, straggler ratio) by timing
         syk_apply_H on this Hamiltonian; keeps the fastest plan.  With
@@ -185,8 +185,9 @@ class Terms:
             json.dump(cache, open(cache_path, "w"), indent=1)
         return res
 
-    def replan(self, l2_budget_bytes: int = 2 << 20, straggler_ratio: float = 1.5):
-        """Regroup the matvec passes (L2 budget in bytes, straggler cost ratio)."""
+    def replan(self, l2_budget_bytes: int = 0, straggler_ratio: float = 0.0):
+        """Regroup the matvec passes (L2 budget in bytes, straggler cost ratio);
+        l2_budget_bytes = 0 restores the dtype's default plan."""
         L.check(self._lib.syk_terms_replan(self._h, int(l2_budget_bytes), float(straggler_ratio)))
         info = L.TermsInfo()
         L.check(self._lib.syk_terms_get_info(self._h, C.byref(info)))

@@ -43,6 +43,8 @@ struct MV {
   double* partial;                    // Lanczos: Re <v_j, w> per block
   const KScalars* sc;
   int j;
+  unsigned long long* sched = nullptr;  // complex64 EPI_STORE: [0] next item, [1] CTAs finished
+  uint32_t ny = 1;                      // complex64 EPI_STORE: states in this launch
 };
 
 // Epilogue shared by the first Lanczos pass and the second (regenerating)
@@ -326,23 +328,45 @@ __global__ void __launch_bounds__(256) k_matvec_tma(MV<Real> p, int* err_flag) {
 // ---------------------------------------------------------------------------
 // complex64 matvec, warp-specialised TMA pipeline (vectors of >= 2048 amplitudes).
 //
-// Warp 8 is the producer: its lane 0 streams input tiles (one 16 KiB bulk
-// copy per (tile, term) job) into S shared-memory stages, waiting on an
-// "empty" mbarrier per stage before reusing it.  Warps 0-7 consume: each
-// lane owns two neighbouring amplitudes in four rows of its warp's 256-
-// amplitude slice (m = tile + 256 w + 64 r + 2 lane + {0, 1}), reads both
+// Warp kConsumerWarps is the producer: its lane 0 streams input tiles (one
+// 16 KiB bulk copy per (tile, term) job) into S shared-memory stages, waiting
+// on an "empty" mbarrier per stage before reusing it.  Warps 0..kConsumerWarps-1
+// consume: each lane owns two neighbouring amplitudes in kRows rows of its
+// warp's slice (m = tile + 64 kRows w + 64 r + 2 lane + {0, 1}), reads both
 // inputs of a term with one 16-byte shared load, and signals the stage free
 // with one arrive per warp.  Terms of a pass are sorted by class
 // (imag, x & 1, z & 1) so that the pair swap (x & 1) and the sign difference
-// inside the pair (z & 1) are compile-time; the row permutation (bits 6-7 of
-// x) is a warp-uniform switch.  Every wait is bounded (1 s); on a timeout the
-// CTA records the error, stops issuing, drains its copies and exits.
+// inside the pair (z & 1) are compile-time; the row permutation (bits 6-8 of
+// x) is a warp-uniform switch.
+//
+// Tile order.  The work items of a launch are (state, tile) pairs in the
+// pass's super-tile order.  Passes that only store their sum (EPI_STORE) start
+// each CTA at item blockIdx.x and then take items gridDim.x + p.sched[0]++
+// from a device-wide counter, one claim prefetched per CTA (so a launch with
+// no more items than CTAs does no extra work), so every CTA works within the
+// same few super-tiles and the pass's inputs
+// stay L2-resident for the whole launch; with a static round-robin split the
+// CTAs drift apart by thousands of tiles over a long pass and evict each
+// other's super-tiles.  The last CTA to finish returns the counter to zero
+// (p.sched[1] counts finished CTAs), so launches that use one counter must
+// not overlap on the GPU.  Passes with a Lanczos epilogue keep the static
+// split: their per-CTA dot-product partials then cover a fixed set of tiles
+// and the reduction is reproducible bit for bit.  The producer publishes each
+// item in a small shared ring (s_item) before the stage barrier of the tile's
+// first job completes, which orders it for the consumers; an item >= n_items
+// ends the CTA's stream.  Every wait is bounded (1 s); on a timeout the CTA
+// records the error, stops issuing, drains its copies and exits.
 template <int EPI, bool ACCUM, int S>
 __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_matvec_c64(MV<float> p, int* err_flag) {
   constexpr uint32_t kTileBytes = (1u << kTileBits) * 8u;
+  constexpr bool kQueue = EPI == EPI_STORE;
+  constexpr int kRing = 8;  // items in flight between producer and consumers: at most S + 1
+  static_assert(kRing > S + 1, "item ring too small for the stage count");
+  constexpr uint64_t kEnd = ~0ull;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ uint64_t s_item[kRing];
   __shared__ int s_err;
   if (EPI == EPI_LANCZOS && p.sc->m_eff <= p.j) return;
   if (EPI == EPI_RECUR && p.j + 1 >= p.sc->m_eff) return;
@@ -351,12 +375,23 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
   for (int c = 0; c < 9; ++c) cls[c] = p.pass->cls[c];
   const int t0 = cls[0], t1 = cls[8];
   const int Tp = t1 - t0;
-  const uint64_t soff = static_cast<uint64_t>(blockIdx.y) * p.D;
-  const float2* __restrict__ psi = p.psi + soff;
-  float2* __restrict__ out = p.out + soff;
+  const bool feed = Tp > 0 || ACCUM;  // the producer has jobs (else the sum is zero)
+  const bool queue = kQueue && feed;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t ntiles = static_cast<uint32_t>(p.D >> kTileBits);
-  const uint32_t my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x - 1) / gridDim.x + 1 : 0;
+  const uint32_t ntiles = static_cast<uint32_t>(p.D >> kTileBits);  // a power of two
+  const uint32_t tshift = 31u - static_cast<uint32_t>(__clz(ntiles));
+  // EPI_STORE launches are one-dimensional over p.ny states; the others use blockIdx.y.
+  const uint64_t n_items = kQueue ? (static_cast<uint64_t>(p.ny) << tshift) : ntiles;
+  const uint64_t ybase = kQueue ? 0ull : blockIdx.y;
+  auto static_item = [&](uint64_t k) -> uint64_t {
+    const uint64_t it = blockIdx.x + k * gridDim.x;
+    return it < n_items ? it : kEnd;
+  };
+  auto tile_base = [&](uint64_t item) -> uint32_t {
+    const uint32_t bt = static_cast<uint32_t>(item) & (ntiles - 1u);
+    return __ldg(&p.pass->dep[0][bt & 255u]) | __ldg(&p.pass->dep[1][(bt >> 8) & 255u]) |
+           __ldg(&p.pass->dep[2][(bt >> 16) & 255u]);
+  };
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(smem_u32(&full_bar[i]), 1);
@@ -366,30 +401,39 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
     fence_mbar_init();
   }
   __syncthreads();
-  auto tile_base = [&](uint32_t k) -> uint32_t {
-    const uint32_t bt = blockIdx.x + k * gridDim.x;
-    return __ldg(&p.pass->dep[0][bt & 255u]) | __ldg(&p.pass->dep[1][(bt >> 8) & 255u]) |
-           __ldg(&p.pass->dep[2][(bt >> 16) & 255u]);
-  };
   double part = 0.0;
   if (warp == kConsumerWarps) {
     // ---------------- producer ----------------
-    if (lane == 0 && (Tp > 0 || ACCUM)) {
+    if (lane == 0 && feed) {
       const uint32_t smem0 = smem_u32(smem_raw);
       const uint64_t keep = l2_policy_evict_last();   // input tiles: re-read by the pass's other terms
       const uint64_t stream = l2_policy_evict_first();  // the output tile: read once per pass
       uint64_t q = 0, issued = 0;
+      uint64_t next = static_item(0);  // the first item is blockIdx.x in both orders
       // Job stream per tile: [the tile of `out` (ACCUM only)] then one input tile per term.
-      for (uint32_t k = 0; k < my_tiles && !*(volatile int*)&s_err; ++k) {
-        const uint32_t tb = tile_base(k);
+      for (uint64_t k = 0; !*(volatile int*)&s_err; ++k) {
+        const uint64_t item = next < n_items ? next : kEnd;
+        if (item != kEnd) next = queue ? gridDim.x + atomicAdd(p.sched, 1ull) : static_item(k + 1);
+        if (item == kEnd) {  // end marker: an arrive without bytes on the next stage
+          const uint32_t stg = static_cast<uint32_t>(q % S);
+          if (q >= S && !mbar_wait_bounded(smem_u32(&empty_bar[stg]), static_cast<uint32_t>(((q / S) - 1) & 1),
+                                           &s_err))
+            break;
+          s_item[k % kRing] = kEnd;
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[stg])) : "memory");
+          break;
+        }
+        const uint64_t soff = (ybase + (item >> tshift)) * p.D;
+        const uint32_t tb = tile_base(item);
         for (int tt = ACCUM ? t0 - 1 : t0; tt < t1 && !*(volatile int*)&s_err; ++tt, ++q) {
           const uint32_t stg = static_cast<uint32_t>(q % S);
           if (q >= S && !mbar_wait_bounded(smem_u32(&empty_bar[stg]), static_cast<uint32_t>(((q / S) - 1) & 1),
                                            &s_err))
             break;
+          if (tt == (ACCUM ? t0 - 1 : t0)) s_item[k % kRing] = item;
           const bool phi = ACCUM && tt < t0;
           const uint2 xf = phi ? make_uint2(0u, 0u) : make_uint2(__ldg(&p.rec[tt].x), __ldg(&p.rec[tt].flags));
-          const float2* src = phi ? out + tb : psi + (tb ^ (xf.x & ~((1u << kTileBits) - 1u)));
+          const float2* src = phi ? p.out + soff + tb : p.psi + soff + (tb ^ (xf.x & ~((1u << kTileBits) - 1u)));
           const uint32_t bar = smem_u32(&full_bar[stg]);
           mbar_expect_tx(bar, kTileBytes);
           bulk_g2s_hint(smem0 + stg * kTileBytes, src, kTileBytes, bar, (phi || (xf.y & 1u)) ? stream : keep);
@@ -402,6 +446,14 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
           const uint64_t ts = globaltimer_ns();
           while (!mbar_try_wait(bar, static_cast<uint32_t>((qq / S) & 1)) && globaltimer_ns() - ts < kWaitLimitNs) {
           }
+        }
+      }
+      if (queue) {  // this CTA claims no more items; the last one to get here resets the counter
+        __threadfence();
+        if (atomicAdd(p.sched + 1, 1ull) == gridDim.x - 1ull) {
+          __threadfence();
+          atomicExch(p.sched, 0ull);
+          atomicExch(p.sched + 1, 0ull);
         }
       }
     }
@@ -418,11 +470,20 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
     }
     const uint32_t pair_part = warp * (64u * kRows) + 2u * lane;
     const uint64_t out_pol = l2_policy_evict_first();  // output tiles are not re-read within the pass
-    const float4* psi4 = reinterpret_cast<const float4*>(psi);
-    float4* out4 = reinterpret_cast<float4*>(out);
     uint64_t q = 0;
-    for (uint32_t k = 0; k < my_tiles; ++k) {
-      const uint32_t mt = tile_base(k) + pair_part;  // amplitude of row 0, even
+    for (uint64_t k = 0;; ++k) {
+      uint64_t item;
+      if (feed) {  // the item rides with the tile's first job
+        if (!mbar_wait_bounded(smem_u32(&full_bar[q % S]), static_cast<uint32_t>((q / S) & 1), &s_err)) break;
+        item = *reinterpret_cast<volatile uint64_t*>(&s_item[k % kRing]);
+      } else {
+        item = static_item(k);
+      }
+      if (item >= n_items) break;
+      const uint64_t soff = (ybase + (item >> tshift)) * p.D;
+      const float4* psi4 = reinterpret_cast<const float4*>(p.psi + soff);
+      float4* out4 = reinterpret_cast<float4*>(p.out + soff);
+      const uint32_t mt = tile_base(item) + pair_part;  // amplitude of row 0, even
       float4 prev[kRows];
       if (ACCUM) {  // the producer's first job of the tile is this tile of `out`
         const uint32_t stg = static_cast<uint32_t>(q % S);
@@ -877,7 +938,16 @@ void launch_pass(const syk_terms* h, const Shape& s, const MV<Real>& q, unsigned
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn)));
         configured.fetch_or(bit);
       }
-      k_matvec_c64<EPI, ACCUM, kStagesC64><<<dim3(s.grid, gy), 32 * (kConsumerWarps + 1), dyn, st>>>(q, h->d_err);
+      if (EPI == EPI_STORE) {  // one-dimensional over (state, tile) items taken from the handle's counter
+        MV<Real> qq = q;
+        qq.sched = h->d_sched;
+        qq.ny = gy;
+        const uint64_t items = (static_cast<uint64_t>(h->D) >> kTileBits) * gy;
+        const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(items, static_cast<uint64_t>(h->n_sm) * kC64CtasPerSm));
+        k_matvec_c64<EPI, ACCUM, kStagesC64><<<grid, 32 * (kConsumerWarps + 1), dyn, st>>>(qq, h->d_err);
+      } else {
+        k_matvec_c64<EPI, ACCUM, kStagesC64><<<dim3(s.grid, gy), 32 * (kConsumerWarps + 1), dyn, st>>>(q, h->d_err);
+      }
       return;
     }
   }

@@ -144,6 +144,7 @@ void upload_table(syk_terms* h) {
     h->d_coef[1] = d + (hc1 - p);
     h->d_passes = reinterpret_cast<syk::PassPlan*>(d + (hp - p));
     h->d_err = reinterpret_cast<int*>(d + (hp - p) + pass_bytes);  // zeroed with the host image
+    h->d_sched = reinterpret_cast<unsigned long long*>(d + (hp - p) + pass_bytes + 64);  // likewise
     h->d_termf[0] = reinterpret_cast<syk::TermF*>(d + (hr0 - p));
     h->d_termf[1] = reinterpret_cast<syk::TermF*>(d + (hr1 - p));
     h->d_zi = reinterpret_cast<uint32_t*>(d + (reinterpret_cast<char*>(hzi) - p));
@@ -186,7 +187,8 @@ int syk_build_terms(int N, int64_t T, const int32_t* quads, const double* J, int
     syk::compile_terms(N, rep, T, quads, J, h->terms, h->n_real, h->n_xgroups);
     for (const auto& t : h->terms) h->sum_abs += std::max(std::fabs(t.coef[0]), std::fabs(t.coef[1]));
     for (int n = 0; n < N; ++n) h->chi[n] = syk::compile_chi(N, rep, n);
-    h->passes = syk::plan_passes(h->terms, h->L, syk::elem_bytes(dtype), syk::kL2Budget, syk::kDefaultHbmRatio);
+    h->passes = syk::plan_passes(h->terms, h->L, syk::elem_bytes(dtype), syk::default_l2_budget(dtype),
+                                   syk::default_hbm_ratio(dtype));
     SYK_CUDA(cudaGetDevice(&h->device));
     SYK_CUDA(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device));
     upload_table(h.get());
@@ -223,8 +225,12 @@ int syk_terms_get_info(const syk_terms_t* h, syk_terms_info* info) {
 int syk_terms_replan(syk_terms_t* h, size_t l2_budget_bytes, double straggler_ratio) {
   return guarded("syk_terms_replan", [&] {
     check_handle(h);
-    SYK_REQUIRE(l2_budget_bytes >= 4096, "l2_budget_bytes must be >= 4096");
+    SYK_REQUIRE(l2_budget_bytes == 0 || l2_budget_bytes >= 4096, "l2_budget_bytes must be 0 or >= 4096");
     SYK_REQUIRE(std::isfinite(straggler_ratio) && straggler_ratio >= 0, "straggler_ratio must be >= 0");
+    if (l2_budget_bytes == 0) {  // the default plan of the handle's dtype
+      l2_budget_bytes = syk::default_l2_budget(h->dtype);
+      straggler_ratio = syk::default_hbm_ratio(h->dtype);
+    }
     h->passes = syk::plan_passes(h->terms, h->L, syk::elem_bytes(h->dtype), l2_budget_bytes, straggler_ratio);
     upload_table(h);
   });

@@ -14,7 +14,6 @@ namespace syk {
 
 constexpr int kMaxKrylov = 64;   // largest Krylov dimension per substep
 constexpr int kTileBits = 11;    // amplitudes per matvec block tile = 2^11 (8 warps x 8 rows x 32 lanes)
-constexpr size_t kL2Budget = size_t(2) << 20;  // default bytes of a block vector kept L2-resident per pass
 constexpr int kMaxPartials = 2048;  // per-state reduction partials (>= any grid.x)
 
 struct Error : std::runtime_error {
@@ -78,7 +77,13 @@ struct alignas(16) TermF {
 // Reorders `terms` by pass and returns the passes.
 std::vector<PassPlan> plan_passes(std::vector<BlockString>& terms, int L, size_t elem_bytes, size_t l2_budget,
                                    double hbm_ratio);
-constexpr double kDefaultHbmRatio = 1.5;  // best of a B300 sweep at N = 64 (budget x ratio grid)
+// Default pass plan per dtype: the best of B300 budget x ratio sweeps at
+// N = 64.  complex64 passes draw their tiles from a shared counter, so every
+// CTA stays inside the same super-tiles and large (L2/4) super-tiles stay
+// resident; complex128 passes split tiles statically and are FP64-bound, so
+// they keep small super-tiles.
+inline size_t default_l2_budget(int dtype) { return dtype == SYK_C64 ? size_t(32) << 20 : size_t(2) << 20; }
+inline double default_hbm_ratio(int dtype) { return dtype == SYK_C64 ? 3.0 : 1.5; }
 
 // Device view of a compiled term table, in compute precision Real.
 template <typename Real>
@@ -105,6 +110,7 @@ struct syk_terms {
   syk::PassPlan* d_passes = nullptr;
   syk::TermF* d_termf[2] = {nullptr, nullptr};  // complex64 handles: packed terms per block
   int* d_err = nullptr;  // set by a kernel whose bounded wait expired
+  unsigned long long* d_sched = nullptr;  // complex64 matvec tile counter pair (zero between launches)
   uint32_t* d_zi = nullptr;  // z | (imag << 31) per term (batched engine)
   int n_sm = 148;
   syk_terms() = default;

@@ -95,8 +95,9 @@ def test_apply_H_multipass_plans_N32(syk, dtype):
     with syk.Terms(N, q, J, dtype=dtype) as h:
         assert h.info["n_passes"] == 1
         seen = set()
-        for budget in (1 << 30, 1 << 16, 1 << 14, 4096):
-            npass = h.replan(budget)
+        # plain passes, passes with straggler terms, the plain-order fallback, the default plan
+        for budget, ratio in ((1 << 30, 0.0), (1 << 16, 3.0), (1 << 14, 1.5), (1 << 14, 0.0), (4096, 0.0), (0, 0.0)):
+            npass = h.replan(budget, ratio)
             seen.add(npass)
             ex = h.export()
             assert len(ex["x"]) == h.n_terms
@@ -129,7 +130,7 @@ def test_krylov_multipass_N32(syk):
     x = rand_vec(1 << 15, 14)
     ref = dyn.evolve_sparse(Hc, 0.5 + 2.0j, x)
     with syk.Terms(N, q, J, dtype="c128") as h:
-        h.replan(1 << 16)
+        h.replan(1 << 16, 3.0)
         assert h.info["n_passes"] >= 2
         for two_pass in (False, True):
             y, _ = h.krylov_evolve(to_dev(x, "c128"), 0, 0.5, 2.0, tol=1e-13, two_pass=two_pass)
