@@ -470,11 +470,12 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
     }
     const uint32_t pair_part = warp * (64u * kRows) + 2u * lane;
     const uint64_t out_pol = l2_policy_evict_first();  // output tiles are not re-read within the pass
-    uint64_t q = 0;
+    StageRing<S> ring;
+    uint4 d = Tp > 0 ? __ldg(reinterpret_cast<const uint4*>(p.rec + t0)) : make_uint4(0u, 0u, 0u, 0u);
     for (uint64_t k = 0;; ++k) {
       uint64_t item;
       if (feed) {  // the item rides with the tile's first job
-        if (!mbar_wait_bounded(smem_u32(&full_bar[q % S]), static_cast<uint32_t>((q / S) & 1), &s_err)) break;
+        if (!mbar_wait_bounded(smem_u32(&full_bar[ring.stg]), ring.ph, &s_err)) break;
         item = *reinterpret_cast<volatile uint64_t*>(&s_item[k % kRing]);
       } else {
         item = static_item(k);
@@ -484,38 +485,40 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
       const float4* psi4 = reinterpret_cast<const float4*>(p.psi + soff);
       float4* out4 = reinterpret_cast<float4*>(p.out + soff);
       const uint32_t mt = tile_base(item) + pair_part;  // amplitude of row 0, even
-      float4 prev[kRows];
-      if (ACCUM) {  // the producer's first job of the tile is this tile of `out`
-        const uint32_t stg = static_cast<uint32_t>(q % S);
-        const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), static_cast<uint32_t>((q / S) & 1), &s_err);
+      // The sum starts from the partial sum of the earlier passes (ACCUM: the
+      // producer's first job of the tile is this tile of `out`), else from 0.
+      float a[kRows][4];
+      if (ACCUM) {
+        const uint32_t stg = ring.stg;
+        const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), ring.ph, &s_err);
         const float4* t4 = reinterpret_cast<const float4*>(smem_raw + stg * kTileBytes);
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) prev[r] = ok ? t4[(pair_part >> 1) + 32u * r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int r = 0; r < kRows; ++r) {
+          const float4 pv = ok ? t4[(pair_part >> 1) + 32u * r] : make_float4(0.f, 0.f, 0.f, 0.f);
+          a[r][0] = pv.x;
+          a[r][1] = pv.y;
+          a[r][2] = pv.z;
+          a[r][3] = pv.w;
+        }
         __syncwarp();
         if (lane == 0 && ok)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty_bar[stg])) : "memory");
-        ++q;
-      }
-      float a[kRows][4];
+        ring.next();
+      } else {
 #pragma unroll
-      for (int r = 0; r < kRows; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
-      c64_consume<false, false, false, S>(cls[0], cls[1], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<false, false, true, S>(cls[1], cls[2], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<false, true, false, S>(cls[2], cls[3], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<false, true, true, S>(cls[3], cls[4], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<true, false, false, S>(cls[4], cls[5], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<true, false, true, S>(cls[5], cls[6], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<true, true, false, S>(cls[6], cls[7], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<true, true, true, S>(cls[7], cls[8], q, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        for (int r = 0; r < kRows; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
+      }
+      c64_consume<false, false, false, S>(cls[0], cls[1], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<false, false, true, S>(cls[1], cls[2], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<false, true, false, S>(cls[2], cls[3], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<false, true, true, S>(cls[3], cls[4], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<true, false, false, S>(cls[4], cls[5], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<true, false, true, S>(cls[5], cls[6], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<true, true, false, S>(cls[6], cls[7], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_consume<true, true, true, S>(cls[7], cls[8], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
         const uint32_t i4 = (mt >> 1) + 32u * r;
-        if (ACCUM) {
-          a[r][0] += prev[r].x;
-          a[r][1] += prev[r].y;
-          a[r][2] += prev[r].z;
-          a[r][3] += prev[r].w;
-        }
         if (EPI == EPI_STORE) {
           st_f4_hint(out4 + i4, make_float4(a[r][0], a[r][1], a[r][2], a[r][3]), out_pol);
         } else {

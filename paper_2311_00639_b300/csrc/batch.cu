@@ -464,7 +464,8 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
     const float4* v4 = reinterpret_cast<const float4*>(v);
     const float4* vp4 = reinterpret_cast<const float4*>(vp);
     float4* w4 = reinterpret_cast<float4*>(w);
-    uint64_t q = 0;
+    StageRing<S> ring;
+    uint4 d = T > 0 ? __ldg(reinterpret_cast<const uint4*>(rec)) : make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t k = 0; k < my_tiles; ++k) {
       const uint32_t mt = ((tl + k * rg.y) << kTileBits) + pair_part;
       float acc[kRows][4];
@@ -472,14 +473,14 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
       for (int r = 0; r < kRows; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
       for (int pz = 0; pz < s.n_passes; ++pz) {
         const int* cl = s.passes[pz].cls;
-        c64_consume<false, false, false, S>(cl[0], cl[1], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<false, false, true, S>(cl[1], cl[2], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<false, true, false, S>(cl[2], cl[3], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<false, true, true, S>(cl[3], cl[4], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<true, false, false, S>(cl[4], cl[5], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<true, false, true, S>(cl[5], cl[6], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<true, true, false, S>(cl[6], cl[7], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<true, true, true, S>(cl[7], cl[8], q, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<false, false, false, S>(cl[0], cl[1], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<false, false, true, S>(cl[1], cl[2], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<false, true, false, S>(cl[2], cl[3], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<false, true, true, S>(cl[3], cl[4], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<true, false, false, S>(cl[4], cl[5], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<true, false, true, S>(cl[5], cl[6], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<true, true, false, S>(cl[6], cl[7], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+        c64_consume<true, true, true, S>(cl[7], cl[8], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
       }
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {

@@ -106,12 +106,20 @@ constexpr int kRows = SYK_C64_ROWS;
 constexpr int kConsumerWarps = (1 << kTileBits) / (64 * kRows);
 constexpr uint32_t kRowMask = static_cast<uint32_t>(kRows - 1) << 6;  // amplitude bits chosen by the row
 constexpr uint32_t kPairXMask = 0x7FEu & ~kRowMask;                    // in-tile flip bits applied per lane
+// 3 stages x 4 CTAs per SM (96 registers a thread) beat 4 x 3 on B300: the
+// extra consumer warps hide more of the bulk-copy latency for the same bytes
+// in flight per SM.
 #ifndef SYK_C64_STAGES
-#define SYK_C64_STAGES 4
+#define SYK_C64_STAGES 3
 #endif
 constexpr int kStagesC64 = SYK_C64_STAGES;
-// CTAs per SM: shared memory holds S 16 KiB stages each (<= 227 KiB per SM), at most 3.
-constexpr int kC64CtasPerSm = (227 / (16 * kStagesC64 + 2)) < 3 ? (227 / (16 * kStagesC64 + 2)) : 3;
+#ifndef SYK_C64_MAX_CTAS
+#define SYK_C64_MAX_CTAS 4
+#endif
+// CTAs per SM: shared memory holds S 16 KiB stages each (<= 227 KiB per SM),
+// at most SYK_C64_MAX_CTAS (the register budget of __launch_bounds__).
+constexpr int kC64CtasPerSm = (227 / (16 * kStagesC64 + 2)) < SYK_C64_MAX_CTAS ? (227 / (16 * kStagesC64 + 2))
+                                                                               : SYK_C64_MAX_CTAS;
 
 template <bool IMAG, bool XS, bool ZS, int XR>
 __device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t pa2, const float (&c)[kRows],
@@ -138,18 +146,36 @@ __device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t
   }
 }
 
+// A consumer's position in the stage ring: the stage of its next job and the
+// mbarrier phase parity that job completes.
+template <int S>
+struct StageRing {
+  uint32_t stg = 0, ph = 0;
+  __device__ __forceinline__ void next() {
+    if (++stg == static_cast<uint32_t>(S)) {
+      stg = 0;
+      ph ^= 1u;
+    }
+  }
+};
+
+// Consume terms [tb0, tb1) of the current tile.  `d` holds the record of
+// term tb0 on entry and of the term after tb1 - 1 on exit: each iteration
+// loads the next record (wrapping from tend - 1 to tfirst, the term range of
+// one tile) so that its L1 latency overlaps the current term.
 template <bool IMAG, bool XS, bool ZS, int S>
-__device__ __forceinline__ void c64_consume(int tb0, int tb1, uint64_t& q, float (&a)[kRows][4],
-                                            const TermF* __restrict__ rec, uint32_t mt, uint32_t pair_part,
-                                            const unsigned char* smem, uint64_t* full_bar, uint64_t* empty_bar,
-                                            volatile int* s_err, uint32_t lane) {
-  for (int tt = tb0; tt < tb1; ++tt, ++q) {
-    const uint32_t stg = static_cast<uint32_t>(q % S);
-    const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), static_cast<uint32_t>((q / S) & 1), s_err);
+__device__ __forceinline__ void c64_consume(int tb0, int tb1, int tfirst, int tend, uint4& d, StageRing<S>& ring,
+                                            float (&a)[kRows][4], const TermF* __restrict__ rec, uint32_t mt,
+                                            uint32_t pair_part, const unsigned char* smem, uint64_t* full_bar,
+                                            uint64_t* empty_bar, volatile int* s_err, uint32_t lane) {
+  for (int tt = tb0; tt < tb1; ++tt, ring.next()) {
+    const uint4 cur = d;
+    d = __ldg(reinterpret_cast<const uint4*>(rec + (tt + 1 < tend ? tt + 1 : tfirst)));
+    const uint32_t stg = ring.stg;
+    const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), ring.ph, s_err);
     if (ok) {
-      const uint4 d = __ldg(reinterpret_cast<const uint4*>(rec + tt));
-      const uint32_t x = d.x, z = d.y;
-      const uint32_t cb = d.z;
+      const uint32_t x = cur.x, z = cur.y;
+      const uint32_t cb = cur.z;
       // sign (-1)^{popc(z & m)} of row r: the lane/warp/tile part popc(z & mt)
       // and the row part popc(z & 64 r) = parity of (z >> 6) & r, folded into
       // the coefficient's sign bit.
