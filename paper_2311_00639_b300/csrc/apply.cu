@@ -425,19 +425,20 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
         }
         const uint64_t soff = (ybase + (item >> tshift)) * p.D;
         const uint32_t tb = tile_base(item);
-        for (int tt = ACCUM ? t0 - 1 : t0; tt < t1 && !*(volatile int*)&s_err; ++tt, ++q) {
+        for (int tt = ACCUM ? t0 - 1 : t0; tt < t1 && !*(volatile int*)&s_err; ++tt) {
+          const bool phi = ACCUM && tt < t0;
+          const uint2 xf = phi ? make_uint2(0u, 0u) : make_uint2(__ldg(&p.rec[tt].x), __ldg(&p.rec[tt].flags));
+          if (!phi && !(xf.y & kTermRunStart)) continue;  // the run's tile is already staged
           const uint32_t stg = static_cast<uint32_t>(q % S);
           if (q >= S && !mbar_wait_bounded(smem_u32(&empty_bar[stg]), static_cast<uint32_t>(((q / S) - 1) & 1),
                                            &s_err))
             break;
           if (tt == (ACCUM ? t0 - 1 : t0)) s_item[k % kRing] = item;
-          const bool phi = ACCUM && tt < t0;
-          const uint2 xf = phi ? make_uint2(0u, 0u) : make_uint2(__ldg(&p.rec[tt].x), __ldg(&p.rec[tt].flags));
           const float2* src = phi ? p.out + soff + tb : p.psi + soff + (tb ^ (xf.x & ~((1u << kTileBits) - 1u)));
           const uint32_t bar = smem_u32(&full_bar[stg]);
           mbar_expect_tx(bar, kTileBytes);
-          bulk_g2s_hint(smem0 + stg * kTileBytes, src, kTileBytes, bar, (phi || (xf.y & 1u)) ? stream : keep);
-          issued = q + 1;
+          bulk_g2s_hint(smem0 + stg * kTileBytes, src, kTileBytes, bar, (phi || (xf.y & kTermStraggler)) ? stream : keep);
+          issued = ++q;
         }
       }
       if (s_err) {  // drain: the last copy issued into each stage must land before exit
@@ -508,14 +509,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
 #pragma unroll
         for (int r = 0; r < kRows; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
       }
-      c64_consume<false, false, false, S>(cls[0], cls[1], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<false, false, true, S>(cls[1], cls[2], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<false, true, false, S>(cls[2], cls[3], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<false, true, true, S>(cls[3], cls[4], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<true, false, false, S>(cls[4], cls[5], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<true, false, true, S>(cls[5], cls[6], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<true, true, false, S>(cls[6], cls[7], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      c64_consume<true, true, true, S>(cls[7], cls[8], t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_terms<S>(t0, t1, t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
         const uint32_t i4 = (mt >> 1) + 32u * r;

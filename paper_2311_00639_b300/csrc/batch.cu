@@ -439,14 +439,16 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
       uint32_t q = 0, issued = 0;
       for (uint32_t k = 0; k < my_tiles && !*(volatile int*)&s_err; ++k) {
         const uint32_t tb = (tl + k * rg.y) << kTileBits;
-        for (int tt = 0; tt < T && !*(volatile int*)&s_err; ++tt, ++q) {
+        for (int tt = 0; tt < T && !*(volatile int*)&s_err; ++tt) {
+          const uint2 xf = make_uint2(__ldg(&rec[tt].x), __ldg(&rec[tt].flags));
+          if (!(xf.y & kTermRunStart)) continue;  // the run's tile is already staged
           const uint32_t stg = q % S;
           if (q >= S && !mbar_wait_bounded(smem_u32(&empty_bar[stg]), ((q / S) - 1) & 1u, &s_err)) break;
-          const float2* src = v + (tb ^ (__ldg(&rec[tt].x) & ~((1u << kTileBits) - 1u)));
+          const float2* src = v + (tb ^ (xf.x & ~((1u << kTileBits) - 1u)));
           const uint32_t bar = smem_u32(&full_bar[stg]);
           mbar_expect_tx(bar, kTileBytes);
           bulk_g2s_hint(smem0 + stg * kTileBytes, src, kTileBytes, bar, keep);
-          issued = q + 1;
+          issued = ++q;
         }
       }
       if (s_err) {
@@ -471,17 +473,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
       float acc[kRows][4];
 #pragma unroll
       for (int r = 0; r < kRows; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
-      for (int pz = 0; pz < s.n_passes; ++pz) {
-        const int* cl = s.passes[pz].cls;
-        c64_consume<false, false, false, S>(cl[0], cl[1], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<false, false, true, S>(cl[1], cl[2], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<false, true, false, S>(cl[2], cl[3], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<false, true, true, S>(cl[3], cl[4], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<true, false, false, S>(cl[4], cl[5], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<true, false, true, S>(cl[5], cl[6], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<true, true, false, S>(cl[6], cl[7], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-        c64_consume<true, true, true, S>(cl[7], cl[8], 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
-      }
+      c64_terms<S>(0, T, 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
         const uint32_t i4 = (mt >> 1) + 32u * r;

@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <numeric>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -104,15 +107,34 @@ void upload_table(syk_terms* h) {
     char* hr1 = hr0 + rec_bytes;
     uint32_t* hzi = reinterpret_cast<uint32_t*>(hr1 + rec_bytes);
     for (size_t i = 0; i < n; ++i) hzi[i] = h->terms[i].z | (h->terms[i].imag ? 0x80000000u : 0u);
-    for (size_t i = 0; i < n; ++i)
+    // complex64 records: within each pass, terms that read the same input
+    // tile (equal x >> kTileBits) are made adjacent and flagged as a run.
+    std::vector<size_t> rec_order(n);
+    std::iota(rec_order.begin(), rec_order.end(), size_t(0));
+    auto rec_key = [&](size_t i) {
+      const auto& t = h->terms[i];
+      return std::make_tuple(t.x >> syk::kTileBits, 4 * int(t.imag) + 2 * int(t.x & 1u) + int(t.z & 1u), t.x, t.z);
+    };
+    for (const auto& ps : h->passes)
+      std::stable_sort(rec_order.begin() + ps.t0, rec_order.begin() + ps.t1,
+                       [&](size_t a, size_t b) { return rec_key(a) < rec_key(b); });
+    std::vector<char> pass_end(n + 1, 0);
+    for (const auto& ps : h->passes) pass_end[ps.t1] = 1;
+    for (size_t k = 0; k < n; ++k) {
+      const auto& t = h->terms[rec_order[k]];
+      const uint32_t hi = t.x >> syk::kTileBits;
+      const bool start = k == 0 || pass_end[k] || (h->terms[rec_order[k - 1]].x >> syk::kTileBits) != hi;
+      const bool end = k + 1 == n || pass_end[k + 1] || (h->terms[rec_order[k + 1]].x >> syk::kTileBits) != hi;
       for (int b = 0; b < 2; ++b) {
         syk::TermF r;
-        r.x = h->terms[i].x;
-        r.z = h->terms[i].z;
-        r.c = static_cast<float>(h->terms[i].coef[b]);
-        r.flags = h->terms[i].straggler ? 1u : 0u;
-        std::memcpy((b ? hr1 : hr0) + i * sizeof(syk::TermF), &r, sizeof(r));
+        r.x = t.x;
+        r.z = t.z;
+        r.c = static_cast<float>(t.coef[b]);
+        r.flags = (t.straggler ? syk::kTermStraggler : 0u) | (start ? syk::kTermRunStart : 0u) |
+                  (end ? syk::kTermRunEnd : 0u) | (t.imag ? syk::kTermImag : 0u);
+        std::memcpy((b ? hr1 : hr0) + k * sizeof(syk::TermF), &r, sizeof(r));
       }
+    }
     for (size_t i = 0; i < n; ++i) {
       hx[i] = h->terms[i].x;
       hz[i] = h->terms[i].z;

@@ -67,13 +67,19 @@ struct PassPlan {
   int cls[9] = {};
   uint32_t dep[3][256] = {};
 };
-// Packed complex64 term record (one 16-byte load per term); flags bit 0 marks
-// a straggler (its input tiles come from HBM, fetched with evict-first).
+// Packed complex64 term record (one 16-byte load per term).  The complex64
+// record array keeps each pass's terms together but orders them inside the
+// pass by (x >> kTileBits, class, x, z), so that the terms that read the same
+// input tile (a "run") are adjacent and share one staged copy of it.
 struct alignas(16) TermF {
   uint32_t x, z;
   float c;
   uint32_t flags;
 };
+constexpr uint32_t kTermStraggler = 1u;  // the run's input tiles come from HBM (fetched evict-first)
+constexpr uint32_t kTermRunStart = 2u;   // first term of a run: a new input tile
+constexpr uint32_t kTermRunEnd = 4u;     // last term of a run: its stage is released after it
+constexpr uint32_t kTermImag = 8u;       // coefficient i * c
 // Reorders `terms` by pass and returns the passes.
 std::vector<PassPlan> plan_passes(std::vector<BlockString>& terms, int L, size_t elem_bytes, size_t l2_budget,
                                    double hbm_ratio);

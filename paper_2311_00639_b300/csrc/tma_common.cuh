@@ -159,23 +159,33 @@ struct StageRing {
   }
 };
 
-// Consume terms [tb0, tb1) of the current tile.  `d` holds the record of
-// term tb0 on entry and of the term after tb1 - 1 on exit: each iteration
-// loads the next record (wrapping from tend - 1 to tfirst, the term range of
-// one tile) so that its L1 latency overlaps the current term.
-template <bool IMAG, bool XS, bool ZS, int S>
-__device__ __forceinline__ void c64_consume(int tb0, int tb1, int tfirst, int tend, uint4& d, StageRing<S>& ring,
-                                            float (&a)[kRows][4], const TermF* __restrict__ rec, uint32_t mt,
-                                            uint32_t pair_part, const unsigned char* smem, uint64_t* full_bar,
-                                            uint64_t* empty_bar, volatile int* s_err, uint32_t lane) {
-  for (int tt = tb0; tt < tb1; ++tt, ring.next()) {
+// Apply terms [tb0, tb1) of the current tile.  Consecutive terms with the
+// same input tile (a run, see TermF) read one stage: the warp waits for the
+// stage at the run's first term and releases it after the run's last.  `d`
+// holds the record of term tb0 on entry; each iteration loads the next one
+// (wrapping from tend - 1 to tfirst, the term range of one tile) so that its
+// latency overlaps the current term.  The term's class (imag, x & 1, z & 1)
+// and its row permutation (x bits 6-8) select one of 64 compile-time bodies.
+#define SYK_C64_BODY(k)                                                                                          \
+  case k:                                                                                                        \
+    c64_rows<((k) >> 5) & 1, ((k) >> 4) & 1, ((k) >> 3) & 1, ((k) & 7) % kRows>(t4, pa2, c, a);                 \
+    break;
+#define SYK_C64_BODY8(k) \
+  SYK_C64_BODY(k) SYK_C64_BODY(k + 1) SYK_C64_BODY(k + 2) SYK_C64_BODY(k + 3) SYK_C64_BODY(k + 4) \
+  SYK_C64_BODY(k + 5) SYK_C64_BODY(k + 6) SYK_C64_BODY(k + 7)
+template <int S>
+__device__ __forceinline__ void c64_terms(int tb0, int tb1, int tfirst, int tend, uint4& d, StageRing<S>& ring,
+                                          float (&a)[kRows][4], const TermF* __restrict__ rec, uint32_t mt,
+                                          uint32_t pair_part, const unsigned char* smem, uint64_t* full_bar,
+                                          uint64_t* empty_bar, volatile int* s_err, uint32_t lane) {
+  static_assert(kRows == 8, "the row permutation switch covers x bits 6-8");
+  bool ok = false;
+  for (int tt = tb0; tt < tb1; ++tt) {
     const uint4 cur = d;
     d = __ldg(reinterpret_cast<const uint4*>(rec + (tt + 1 < tend ? tt + 1 : tfirst)));
-    const uint32_t stg = ring.stg;
-    const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), ring.ph, s_err);
+    const uint32_t x = cur.x, z = cur.y, cb = cur.z, fl = cur.w;
+    if (fl & kTermRunStart) ok = mbar_wait_bounded(smem_u32(&full_bar[ring.stg]), ring.ph, s_err);
     if (ok) {
-      const uint32_t x = cur.x, z = cur.y;
-      const uint32_t cb = cur.z;
       // sign (-1)^{popc(z & m)} of row r: the lane/warp/tile part popc(z & mt)
       // and the row part popc(z & 64 r) = parity of (z >> 6) & r, folded into
       // the coefficient's sign bit.
@@ -186,22 +196,29 @@ __device__ __forceinline__ void c64_consume(int tb0, int tb1, int tfirst, int te
       for (int r = 0; r < kRows; ++r)
         c[r] = __uint_as_float(s0 ^ ((r & 1) ? p0 : 0u) ^ ((r & 2) ? p1 : 0u) ^ ((r & 4) ? p2 : 0u));
       const uint32_t pa2 = (pair_part ^ (x & kPairXMask)) >> 1;  // float4 index of the row-0 input pair
-      const float4* t4 = reinterpret_cast<const float4*>(smem + stg * (1u << kTileBits) * 8u);
-      switch ((x & kRowMask) >> 6) {
-        case 0: c64_rows<IMAG, XS, ZS, 0>(t4, pa2, c, a); break;
-        case 1: c64_rows<IMAG, XS, ZS, 1 % kRows>(t4, pa2, c, a); break;
-        case 2: c64_rows<IMAG, XS, ZS, 2 % kRows>(t4, pa2, c, a); break;
-        case 3: c64_rows<IMAG, XS, ZS, 3 % kRows>(t4, pa2, c, a); break;
-        case 4: c64_rows<IMAG, XS, ZS, 4 % kRows>(t4, pa2, c, a); break;
-        case 5: c64_rows<IMAG, XS, ZS, 5 % kRows>(t4, pa2, c, a); break;
-        case 6: c64_rows<IMAG, XS, ZS, 6 % kRows>(t4, pa2, c, a); break;
-        default: c64_rows<IMAG, XS, ZS, 7 % kRows>(t4, pa2, c, a); break;
+      const float4* t4 = reinterpret_cast<const float4*>(smem + ring.stg * (1u << kTileBits) * 8u);
+      const uint32_t body = ((fl & kTermImag) ? 32u : 0u) | ((x & 1u) << 4) | ((z & 1u) << 3) | ((x >> 6) & 7u);
+      switch (body) {
+        SYK_C64_BODY8(0)
+        SYK_C64_BODY8(8)
+        SYK_C64_BODY8(16)
+        SYK_C64_BODY8(24)
+        SYK_C64_BODY8(32)
+        SYK_C64_BODY8(40)
+        SYK_C64_BODY8(48)
+        SYK_C64_BODY8(56)
+        default: break;
       }
     }
-    __syncwarp();
-    if (lane == 0 && ok) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty_bar[stg])) : "memory");
+    if (fl & kTermRunEnd) {
+      __syncwarp();
+      if (lane == 0 && ok) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty_bar[ring.stg])) : "memory");
+      ring.next();
+    }
   }
 }
+#undef SYK_C64_BODY8
+#undef SYK_C64_BODY
 
 }  // namespace
 }  // namespace syk
