@@ -76,6 +76,9 @@ typedef struct {
   int64_t n_passes;    /* matvec passes (term groups with an L2-resident working set) */
   int64_t device_error; /* 1 if a kernel on this handle hit its bounded-wait limit (then results
                            are invalid); reading it synchronises with the device */
+  int64_t n_tile_reads; /* input tiles staged per output tile over all passes of one H psi:
+                           complex64 terms of a pass that read the same tile share one copy;
+                           complex128 stages one tile per term */
 } syk_terms_info;
 
 /*

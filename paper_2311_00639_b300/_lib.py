@@ -17,7 +17,7 @@ class TermsInfo(C.Structure):
     _fields_ = [("N", C.c_int), ("L", C.c_int), ("dtype", C.c_int), ("rep", C.c_int), ("D", C.c_int64),
                 ("n_input", C.c_int64), ("n_terms", C.c_int64), ("n_real", C.c_int64),
                 ("n_xgroups", C.c_int64), ("sum_abs_coef", C.c_double), ("n_passes", C.c_int64),
-                ("device_error", C.c_int64)]
+                ("device_error", C.c_int64), ("n_tile_reads", C.c_int64)]
 
 
 class KrylovParams(C.Structure):

@@ -120,11 +120,13 @@ void upload_table(syk_terms* h) {
                        [&](size_t a, size_t b) { return rec_key(a) < rec_key(b); });
     std::vector<char> pass_end(n + 1, 0);
     for (const auto& ps : h->passes) pass_end[ps.t1] = 1;
+    h->n_runs = 0;
     for (size_t k = 0; k < n; ++k) {
       const auto& t = h->terms[rec_order[k]];
       const uint32_t hi = t.x >> syk::kTileBits;
       const bool start = k == 0 || pass_end[k] || (h->terms[rec_order[k - 1]].x >> syk::kTileBits) != hi;
       const bool end = k + 1 == n || pass_end[k + 1] || (h->terms[rec_order[k + 1]].x >> syk::kTileBits) != hi;
+      h->n_runs += start ? 1 : 0;
       for (int b = 0; b < 2; ++b) {
         syk::TermF r;
         r.x = t.x;
@@ -241,6 +243,7 @@ int syk_terms_get_info(const syk_terms_t* h, syk_terms_info* info) {
     int e = 0;
     SYK_CUDA(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     info->device_error = e;
+    info->n_tile_reads = h->dtype == SYK_C64 ? h->n_runs : static_cast<int64_t>(h->terms.size());
   });
 }
 

@@ -118,6 +118,7 @@ struct syk_terms {
   int* d_err = nullptr;  // set by a kernel whose bounded wait expired
   unsigned long long* d_sched = nullptr;  // complex64 matvec tile counter pair (zero between launches)
   uint32_t* d_zi = nullptr;  // z | (imag << 31) per term (batched engine)
+  int64_t n_runs = 0;  // complex64 record runs (input tiles staged per output tile, all passes)
   int n_sm = 148;
   syk_terms() = default;
   syk_terms(const syk_terms&) = delete;
