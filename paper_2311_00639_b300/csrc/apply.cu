@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
     const uint32_t pair_part = warp * (64u * kRows) + 2u * lane;
     const uint64_t out_pol = l2_policy_evict_first();  // output tiles are not re-read within the pass
     StageRing<S> ring;
-    uint4 d = Tp > 0 ? __ldg(reinterpret_cast<const uint4*>(p.rec + t0)) : make_uint4(0u, 0u, 0u, 0u);
+    uint4 d = make_uint4(0u, 0u, 0u, 0u);
     for (uint64_t k = 0;; ++k) {
       uint64_t item;
       if (feed) {  // the item rides with the tile's first job
@@ -486,6 +486,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
       const float4* psi4 = reinterpret_cast<const float4*>(p.psi + soff);
       float4* out4 = reinterpret_cast<float4*>(p.out + soff);
       const uint32_t mt = tile_base(item) + pair_part;  // amplitude of row 0, even
+      if (Tp > 0) d = __ldg(reinterpret_cast<const uint4*>(p.rec + t0));  // the tile's first term
       // The sum starts from the partial sum of the earlier passes (ACCUM: the
       // producer's first job of the tile is this tile of `out`), else from 0.
       float a[kRows][4];
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
 #pragma unroll
         for (int r = 0; r < kRows; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
       }
-      c64_terms<S>(t0, t1, t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_terms<S>(t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
         const uint32_t i4 = (mt >> 1) + 32u * r;

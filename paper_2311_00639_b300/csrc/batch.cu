@@ -467,13 +467,14 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
     const float4* vp4 = reinterpret_cast<const float4*>(vp);
     float4* w4 = reinterpret_cast<float4*>(w);
     StageRing<S> ring;
-    uint4 d = T > 0 ? __ldg(reinterpret_cast<const uint4*>(rec)) : make_uint4(0u, 0u, 0u, 0u);
+    uint4 d = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t k = 0; k < my_tiles; ++k) {
       const uint32_t mt = ((tl + k * rg.y) << kTileBits) + pair_part;
+      if (T > 0) d = __ldg(reinterpret_cast<const uint4*>(rec));  // the tile's first term
       float acc[kRows][4];
 #pragma unroll
       for (int r = 0; r < kRows; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
-      c64_terms<S>(0, T, 0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_terms<S>(0, T, d, ring, acc, rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
         const uint32_t i4 = (mt >> 1) + 32u * r;

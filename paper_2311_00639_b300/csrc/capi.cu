@@ -91,7 +91,7 @@ void upload_table(syk_terms* h) {
     const size_t rb = h->dtype == SYK_C128 ? 8 : 4;
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
     const size_t pass_bytes = up(h->passes.size() * sizeof(syk::PassPlan));
-    const size_t rec_bytes = up(std::max<size_t>(n, 1) * sizeof(syk::TermF));
+    const size_t rec_bytes = up((n + 1) * sizeof(syk::TermF));  // + one zero record: prefetch past the end
     const size_t zi_bytes = up(std::max<size_t>(n, 1) * 4);
     const size_t bytes = 2 * up(std::max<size_t>(n, 1) * 4) + 2 * up(std::max<size_t>(n, 1) * rb) + pass_bytes + 256 +
                          2 * rec_bytes + zi_bytes;
@@ -133,7 +133,8 @@ void upload_table(syk_terms* h) {
         r.z = t.z;
         r.c = static_cast<float>(t.coef[b]);
         r.flags = (t.straggler ? syk::kTermStraggler : 0u) | (start ? syk::kTermRunStart : 0u) |
-                  (end ? syk::kTermRunEnd : 0u) | (t.imag ? syk::kTermImag : 0u);
+                  (end ? syk::kTermRunEnd : 0u) | (t.imag ? syk::kTermImag : 0u) |
+                  (syk::term_body(t.x, t.z, t.imag) << syk::kTermBodyShift);
         std::memcpy((b ? hr1 : hr0) + k * sizeof(syk::TermF), &r, sizeof(r));
       }
     }

@@ -80,6 +80,12 @@ constexpr uint32_t kTermStraggler = 1u;  // the run's input tiles come from HBM 
 constexpr uint32_t kTermRunStart = 2u;   // first term of a run: a new input tile
 constexpr uint32_t kTermRunEnd = 4u;     // last term of a run: its stage is released after it
 constexpr uint32_t kTermImag = 8u;       // coefficient i * c
+// Bits 8-13 of flags: the consumer body of the term, 32 imag + 16 (x & 1) +
+// 8 (z & 1) + ((x >> 6) & 7) (class and row permutation of the 8-row layout).
+constexpr int kTermBodyShift = 8;
+inline uint32_t term_body(uint32_t x, uint32_t z, bool imag) {
+  return (imag ? 32u : 0u) | ((x & 1u) << 4) | ((z & 1u) << 3) | ((x >> 6) & 7u);
+}
 // Reorders `terms` by pass and returns the passes.
 std::vector<PassPlan> plan_passes(std::vector<BlockString>& terms, int L, size_t elem_bytes, size_t l2_budget,
                                    double hbm_ratio);

@@ -163,9 +163,10 @@ struct StageRing {
 // same input tile (a run, see TermF) read one stage: the warp waits for the
 // stage at the run's first term and releases it after the run's last.  `d`
 // holds the record of term tb0 on entry; each iteration loads the next one
-// (wrapping from tend - 1 to tfirst, the term range of one tile) so that its
-// latency overlaps the current term.  The term's class (imag, x & 1, z & 1)
-// and its row permutation (x bits 6-8) select one of 64 compile-time bodies.
+// (the record array has one spare entry past the last term) so that its
+// latency overlaps the current term.  The term's body index (flags bits
+// 8-13: class imag, x & 1, z & 1 and row permutation x bits 6-8) selects one
+// of 64 compile-time bodies.
 #define SYK_C64_BODY(k)                                                                                          \
   case k:                                                                                                        \
     c64_rows<((k) >> 5) & 1, ((k) >> 4) & 1, ((k) >> 3) & 1, ((k) & 7) % kRows>(t4, pa2, c, a);                 \
@@ -174,17 +175,21 @@ struct StageRing {
   SYK_C64_BODY(k) SYK_C64_BODY(k + 1) SYK_C64_BODY(k + 2) SYK_C64_BODY(k + 3) SYK_C64_BODY(k + 4) \
   SYK_C64_BODY(k + 5) SYK_C64_BODY(k + 6) SYK_C64_BODY(k + 7)
 template <int S>
-__device__ __forceinline__ void c64_terms(int tb0, int tb1, int tfirst, int tend, uint4& d, StageRing<S>& ring,
-                                          float (&a)[kRows][4], const TermF* __restrict__ rec, uint32_t mt,
-                                          uint32_t pair_part, const unsigned char* smem, uint64_t* full_bar,
-                                          uint64_t* empty_bar, volatile int* s_err, uint32_t lane) {
+__device__ __forceinline__ void c64_terms(int tb0, int tb1, uint4& d, StageRing<S>& ring, float (&a)[kRows][4],
+                                          const TermF* __restrict__ rec, uint32_t mt, uint32_t pair_part,
+                                          const unsigned char* smem, uint64_t* full_bar, uint64_t* empty_bar,
+                                          volatile int* s_err, uint32_t lane) {
   static_assert(kRows == 8, "the row permutation switch covers x bits 6-8");
   bool ok = false;
+  const float4* t4 = reinterpret_cast<const float4*>(smem);
   for (int tt = tb0; tt < tb1; ++tt) {
     const uint4 cur = d;
-    d = __ldg(reinterpret_cast<const uint4*>(rec + (tt + 1 < tend ? tt + 1 : tfirst)));
+    d = __ldg(reinterpret_cast<const uint4*>(rec + tt + 1));
     const uint32_t x = cur.x, z = cur.y, cb = cur.z, fl = cur.w;
-    if (fl & kTermRunStart) ok = mbar_wait_bounded(smem_u32(&full_bar[ring.stg]), ring.ph, s_err);
+    if (fl & kTermRunStart) {
+      ok = mbar_wait_bounded(smem_u32(&full_bar[ring.stg]), ring.ph, s_err);
+      t4 = reinterpret_cast<const float4*>(smem + ring.stg * (1u << kTileBits) * 8u);
+    }
     if (ok) {
       // sign (-1)^{popc(z & m)} of row r: the lane/warp/tile part popc(z & mt)
       // and the row part popc(z & 64 r) = parity of (z >> 6) & r, folded into
@@ -196,9 +201,7 @@ __device__ __forceinline__ void c64_terms(int tb0, int tb1, int tfirst, int tend
       for (int r = 0; r < kRows; ++r)
         c[r] = __uint_as_float(s0 ^ ((r & 1) ? p0 : 0u) ^ ((r & 2) ? p1 : 0u) ^ ((r & 4) ? p2 : 0u));
       const uint32_t pa2 = (pair_part ^ (x & kPairXMask)) >> 1;  // float4 index of the row-0 input pair
-      const float4* t4 = reinterpret_cast<const float4*>(smem + ring.stg * (1u << kTileBits) * 8u);
-      const uint32_t body = ((fl & kTermImag) ? 32u : 0u) | ((x & 1u) << 4) | ((z & 1u) << 3) | ((x >> 6) & 7u);
-      switch (body) {
+      switch ((fl >> kTermBodyShift) & 63u) {
         SYK_C64_BODY8(0)
         SYK_C64_BODY8(8)
         SYK_C64_BODY8(16)
