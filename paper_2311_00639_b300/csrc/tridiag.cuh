@@ -27,6 +27,19 @@ __device__ inline double2 phi1_(double re, double im) {
   return make_double2((nr * re + ni * im) / d, (ni * re - nr * im) / d);
 }
 
+// Bits of |v| (IEEE order: for non-negative doubles, integer order = value order).
+__device__ inline long long abs_bits_(double v) { return __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL; }
+
+// |e| <= eps * max(|a|, |b|), eps = 2^-52, decided on bit patterns: FP64
+// instructions are costly on this part and this test runs inside the QL scan.
+// Multiplying by 2^-52 subtracts 52 from the exponent field; when that would
+// leave the normal range the threshold is taken as 0 (deflate only e = 0).
+__device__ inline bool negligible_(double e, double a, double b) {
+  const long long m = max(abs_bits_(a), abs_bits_(b));
+  const long long t = m - (52LL << 52);
+  return abs_bits_(e) <= (t > (1LL << 52) ? t : 0LL);
+}
+
 __device__ inline double warp_sum_(double v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -61,10 +74,8 @@ __device__ void tridiag_warp(KScalars* sc, int m, double z_re, double z_im, doub
     int iter = 0;
     for (;;) {
       int mm = l;
-      for (; mm < n - 1; ++mm) {
-        const double dd = fabs(d[mm]) + fabs(d[mm + 1]);
-        if (fabs(e[mm]) <= DBL_EPSILON * dd) break;
-      }
+      for (; mm < n - 1; ++mm)
+        if (negligible_(e[mm], d[mm], d[mm + 1])) break;
       if (mm == l) break;
       if (++iter > 100) {
         status = 2;
@@ -77,16 +88,22 @@ __device__ void tridiag_warp(KScalars* sc, int m, double z_re, double z_im, doub
       bool deflated = false;
       for (int i = mm - 1; i >= l; --i) {
         const double f = s * e[i], b = c * e[i];
-        r = hypot(f, g);
-        e[i + 1] = r;
-        if (r == 0.0) {
+        // Givens rotation from one reciprocal square root: rho = f^2 + g^2,
+        // r = rho rho^{-1/2}, s = f rho^{-1/2}, c = g rho^{-1/2} (the entries of
+        // a Lanczos T are far from the overflow range).
+        const double rho = fma(f, f, g * g);
+        if (abs_bits_(rho) == 0) {
+          e[i + 1] = 0.0;
           d[i + 1] -= p;
           e[mm] = 0.0;
           deflated = true;
           break;
         }
-        s = f / r;
-        c = g / r;
+        const double inv = rsqrt(rho);
+        r = rho * inv;
+        e[i + 1] = r;
+        s = f * inv;
+        c = g * inv;
         g = d[i + 1] - p;
         r = (d[i] - g) * s + 2.0 * c * b;
         p = s * r;
