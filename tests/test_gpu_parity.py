@@ -174,6 +174,55 @@ def test_apply_H_sampled_rows_large(syk, dtype, N):
         t.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("budget,ratio", [(0, 0.0), (1 << 20, 3.0)])
+def test_apply_H_tile_queue_several_states(syk, budget, ratio):
+    """complex64 passes take (state, tile) items from the device counter: three
+    states of N=44 (1024 tiles each, more items than CTAs, so CTAs claim items
+    across state boundaries), the default plan and a many-pass plan with
+    stragglers; sampled rows of every state against the definition, twice in a
+    row (the counter must come back to zero after each launch)."""
+    t = torch()
+    N = 44
+    q, J, _ = si.sample_sparse_syk(N, 4, r=2)
+    rng = np.random.default_rng(11)
+    with syk.Terms(N, q, J, dtype="c64") as h:
+        npass = h.replan(budget, ratio)
+        assert budget == 0 or npass >= 3
+        D = h.D
+        psi = t.stack([h.random_state(seed=5, state_id=sid, blocks=(0,))[0] for sid in range(3)]).contiguous()
+        rows = np.concatenate([rng.integers(0, D, 600), [0, D - 1]]).astype(np.uint64)
+        idx = t.from_numpy(rows.astype(np.int64)).cuda()
+        for _ in range(2):
+            out = h.apply_H(psi, 0)
+            for sid in range(3):
+                got = out[sid][idx].cpu().numpy()
+                at = lambda b, m, sid=sid: si.philox_state(N, 5, sid, np.uint64(b * D) + m)
+                ref = ham.rows_of_Hpsi(N, q, J, "jw", 0, rows, at)
+                assert rel_err(got, ref) < 2e-5, (sid, npass)
+        assert h.device_error() == 0
+
+
+def test_krylov_c64_plans_agree_N44(syk):
+    """Krylov propagation with tile-queue passes (a 4-pass plan with
+    stragglers: store passes from the counter, the Lanczos epilogue pass split
+    statically) agrees with a single-pass plan, and e^{-iHt} keeps the norm."""
+    t = torch()
+    N = 44
+    q, J, _ = si.sample_sparse_syk(N, 4, r=4)
+    with syk.Terms(N, q, J, dtype="c64") as h:
+        x = h.random_state(seed=9, state_id=1, blocks=(0,))[0]
+        x = x / t.linalg.vector_norm(x)
+        assert h.replan(1 << 20, 3.0) >= 3
+        y_multi, st = h.krylov_evolve(x, 0, 0.0, 1.5, tol=1e-6)
+        h.replan(1 << 30, 0.0)
+        assert h.info["n_passes"] == 1
+        y_one, _ = h.krylov_evolve(x, 0, 0.0, 1.5, tol=1e-6)
+        assert st.matvecs > 0
+        assert abs(t.linalg.vector_norm(y_multi).item() - 1.0) < 1e-5
+        assert (t.max(t.abs(y_multi - y_one)) / t.max(t.abs(y_one))).item() < 1e-5
+        assert h.device_error() == 0
+
+
 # ------------------------------------------------------------ random state --
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_random_state_matches_counter_definition(syk, dtype):
