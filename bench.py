@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-l2", action="store_true")
     ap.add_argument("--no-otoc", action="store_true", help="skip the batched / served OTOC legs")
+    ap.add_argument("--n64-m", type=int, default=10, help="Krylov dimension of the N=64 end-to-end OTOC")
+    ap.add_argument("--n64-two-pass", action="store_true",
+                    help="N=64 OTOC: regenerate the Krylov basis in a second pass (3 vectors) instead of storing "
+                         "m+1 vectors (m=10 stored: 64 s/point; m=20 two-pass: 80 s/point; m=8 stored: 100 s/point)")
     ap.add_argument("--batch-realizations", type=int, default=32)
     ap.add_argument("--batch-states", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=48)
@@ -499,19 +503,23 @@ def otoc_only(args):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     if args.mode == "n64-otoc":
-        # End-to-end OTOC at N=64: complex64 states, FP64 scalars, two-pass Lanczos (m=20),
-        # beta=10, one Philox state, t in {0, 0.5}; both parity blocks.
+        # End-to-end OTOC at N=64: complex64 states, FP64 scalars, Lanczos with a stored
+        # basis of m+1 = 11 vectors (4 + 11 vectors of 16 GiB live; --n64-two-pass keeps 3
+        # by regenerating the basis), beta=10, one Philox state, t in {0, 0.5}; both blocks.
         q, J, _ = si.sample_sparse_syk(args.N, args.k, r=0)
         h = syk.Terms(args.N, q, J, dtype="c64")
         grid = [0.0, 0.5]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        F, o, st = h.otoc(args.N - 1, args.N - 2, 10.0, grid, n_states=1, seed=2024, m=20, two_pass=True)
+        two_pass = args.n64_two_pass
+        F, o, st = h.otoc(args.N - 1, args.N - 2, 10.0, grid, n_states=1, seed=2024, m=args.n64_m,
+                          two_pass=two_pass)
         wall = time.perf_counter() - t0
         line = {"metric": "end-to-end OTOC time per t-point at N=64 (c64 states, FP64 scalars)",
                 "value": wall / len(grid), "unit": "s/point", "higher_is_better": False,
                 "config": {"workload": f"N={args.N}, k={args.k:g}, T={h.n_terms}, beta=10, 1 state, t={grid}, "
-                                       "Lanczos m=20 two-pass", "wall_s": wall, "matvecs": st.matvecs,
+                                       f"Lanczos m={args.n64_m} {'two-pass' if two_pass else 'stored basis'}",
+                           "wall_s": wall, "matvecs": st.matvecs,
                            "substeps": st.substeps, "F": [[z.real, z.imag] for z in F[0]], "otoc": list(o),
                            "s_per_matvec": wall / max(1, st.matvecs)}}
         print(json.dumps(line), flush=True)

@@ -38,6 +38,7 @@ namespace syk {
 namespace {
 
 constexpr int kBlk = 256;          // threads per block
+constexpr int kCtlBlk = 1024;      // threads of the per-slot control block (its vector stages run on one SM)
 constexpr int kMaxBlkPerSlot = 256;  // blocks per slot (partials summed per slot)
 
 enum Stage { S_INIT = 0, S_PART, S_AFTER_U0, S_POINT, S_K1, S_K2, S_K3, S_K4, S_G1, S_G2, S_DONE };
@@ -134,7 +135,7 @@ __device__ __forceinline__ double2 philox_amp(uint64_t g, uint64_t seed, uint64_
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kBlk) k_b_control(BatchArgs a) {
+__global__ void __launch_bounds__(kCtlBlk) k_b_control(BatchArgs a) {
   BSlot& g = a.slots[blockIdx.x];
   __shared__ BSlot s;
   __shared__ int stop;
@@ -683,7 +684,7 @@ void capture_tick(Batch& b) {
                                   static_cast<int>(dyn)));
   SYK_CUDA(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
   const int S = b.max_slots, G = std::max(1, b.total_blocks);
-  k_b_control<Real><<<S, kBlk, 0, b.stream>>>(a);
+  k_b_control<Real><<<S, kCtlBlk, 0, b.stream>>>(a);
   k_b_norm<Real><<<G, kBlk, 0, b.stream>>>(a);
   k_b_scale_first<Real><<<G, kBlk, 0, b.stream>>>(a);
   for (int j = 0; j < b.m; ++j) {
