@@ -725,11 +725,19 @@ int bguard(const char* fn, F&& f) {
 }
 
 void relayout(syk::Batch& b) {
-  // flattened block -> slot map for live slots; dead slots get no blocks
+  // flattened block -> slot map for live slots; dead slots get no blocks.
+  // Slots are laid out in decreasing term count: a matvec block's work is one
+  // tile times the slot's terms, and the block scheduler starts blocks in
+  // index order, so the heaviest tiles start first and the tail is light.
   std::vector<int> blk_slot;
   std::vector<int2> range(b.max_slots, make_int2(0, 0));
-  for (int s = 0; s < b.max_slots; ++s) {
-    if (!b.jobs[s].live) continue;
+  std::vector<int> order;
+  for (int s = 0; s < b.max_slots; ++s)
+    if (b.jobs[s].live) order.push_back(s);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b.jobs[x].job.h->terms.size() > b.jobs[y].job.h->terms.size();
+  });
+  for (const int s : order) {
     const int64_t D = b.jobs[s].job.h->D;
     const bool tiles = b.dtype == SYK_C64 && D >= (int64_t(1) << syk::kTileBits);
     const int nb = static_cast<int>(tiles ? std::min<int64_t>(D >> syk::kTileBits, syk::kMaxBlkPerSlot)
