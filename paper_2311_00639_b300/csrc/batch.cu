@@ -9,9 +9,10 @@
 //             evolution is complete, run the chain's elementwise steps (typical
 //             state, chi_a / chi_b, copies, F(t_n) += <bra|ket>) up to the
 //             next evolution, or mark the job done;
-//   norm, scale_first, m x (matvec+epilogue, axpy_norm, scale_next),
-//   tridiag (one warp per slot), combine  — the Lanczos substep of
-//             syk_krylov_evolve, batched over slots.
+//   norm, scale_first, m x (matvec+epilogue, axpy_norm), tridiag (one warp
+//   per slot), combine  — the Lanczos substep of syk_krylov_evolve, batched
+//             over slots, on an unnormalised basis (basis_scale below): the
+//             last block of a slot to leave axpy_norm finishes the step's beta.
 //
 // The slots of a tick form one flattened grid: slot s owns blocks
 // [blk0[s], blk0[s+1]) (up to 256 blocks of 256 threads, grid-striding over
@@ -85,6 +86,9 @@ struct BatchArgs {
   double* partA;  // [total blocks]
   double* partN;  // [total blocks]
   int* err;       // set when a bounded wait expires
+  double brk;     // Lanczos breakdown threshold, relative to |alpha_j| + beta_{j-1}
+  int* slot_cnt;  // [max slots] blocks of the slot done with k_b_axpy_norm (0 between launches)
+  double* lsc;    // [max slots][2] for the next matvec: s_j = 1 / beta_{j-1}, beta_{j-1} s_{j-1}
 };
 
 template <typename Real>
@@ -101,6 +105,30 @@ __device__ __forceinline__ typename CT<Real>::T* basis(const BSlot& s, int j) {
 }
 
 __device__ __forceinline__ double slot_sum(const double* part, int2 r) { return sum_partials(part + r.x, r.y); }
+
+// The batched Lanczos keeps its basis unnormalised: basis[0] = v_0 (unit) and,
+// for j >= 1, basis[j] = w_{j-1} = beta_{j-1} v_j, so that no pass over the
+// vectors is spent on v_{j+1} = w_j / beta_j.  Every reader folds the scale
+// s_j = 1 / beta_{j-1} (s_0 = 1) into a scalar it applies anyway.  Only call
+// this for betas written by an earlier launch.
+__device__ __forceinline__ double basis_scale(const KScalars* sc, int j) { return j > 0 ? 1.0 / sc->beta[j - 1] : 1.0; }
+
+// Finish Lanczos step j (run by the last block of the slot to leave
+// k_b_axpy_norm(j), after every block's norm partial is visible):
+// beta_j = ||w_j||, the breakdown test (m_eff = j + 1 on breakdown), and the
+// scalars step j + 1's matvec applies: s_{j+1} = 1 / beta_j and
+// beta_j s_j (the coefficient of basis[j]).  All threads of the block call it.
+__device__ __forceinline__ void lanczos_finish_step(const BatchArgs& a, KScalars* sc, int si, int j, int2 rg) {
+  const double b = sqrt(slot_sum(a.partN, rg));
+  if (threadIdx.x == 0) {
+    const double scale = fabs(sc->alpha[j]) + (j > 0 ? sc->beta[j - 1] : 0.0);
+    sc->beta[j] = b;
+    if (!(b > a.brk * fmax(scale, 1e-300))) sc->m_eff = j + 1;
+    a.lsc[2 * si] = 1.0 / b;
+    a.lsc[2 * si + 1] = b * basis_scale(sc, j);
+  }
+}
+
 
 // ----------------------------------------------------------------- control --
 // out = chi (which) in, from block P: out[m] = c (-1)^{popc(z&m)} in[m ^ x].
@@ -362,7 +390,7 @@ __global__ void __launch_bounds__(kBlk) k_b_matvec(BatchArgs a, int j) {
   int2 rg;
   if (!slot_of_block(a, si, tl, rg)) return;
   const BSlot& s = a.slots[si];
-  const KScalars* sc = a.sc + si;
+  KScalars* sc = a.sc + si;
   if (sc->m_eff <= j || j + 1 > static_cast<int>(s.D)) return;
   if (sizeof(Real) == 4 && s.D >= (1u << kTileBits)) return;  // k_b_matvec_c64 handles it
   using C = typename CT<Real>::T;
@@ -370,7 +398,10 @@ __global__ void __launch_bounds__(kBlk) k_b_matvec(BatchArgs a, int j) {
   const C* vp = j > 0 ? basis<Real>(s, j - 1) : nullptr;
   C* w = basis<Real>(s, j + 1);
   const Real* coef = static_cast<const Real*>(s.coef[s.ev_block]);
-  const Real bprev = j > 0 ? static_cast<Real>(sc->beta[j - 1]) : Real(0);
+  // w = s_j H basis[j] - beta_{j-1} s_{j-1} basis[j-1];  Re <v_j, w> = s_j Re <basis[j], w>
+  const double sjd = j > 0 ? a.lsc[2 * si] : 1.0;
+  const Real sj = static_cast<Real>(sjd);
+  const Real bprev = j > 0 ? static_cast<Real>(a.lsc[2 * si + 1]) : Real(0);
   double part = 0.0;
   for (uint32_t m = tl * kBlk + threadIdx.x; m < s.D; m += rg.y * kBlk) {
     Real ar = 0, ai = 0;
@@ -389,14 +420,14 @@ __global__ void __launch_bounds__(kBlk) k_b_matvec(BatchArgs a, int j) {
     C pv = {0, 0};
     if (j > 0) pv = vp[m];
     C o;
-    o.x = fma_(-bprev, pv.x, ar);
-    o.y = fma_(-bprev, pv.y, ai);
+    o.x = fma_(-bprev, pv.x, mul_(sj, ar));
+    o.y = fma_(-bprev, pv.y, mul_(sj, ai));
     w[m] = o;
     const C vv = v[m];
     part += static_cast<double>(vv.x * o.x + vv.y * o.y);
   }
   part = block_sum(part);
-  if (threadIdx.x == 0) a.partA[blockIdx.x] = part;
+  if (threadIdx.x == 0) a.partA[blockIdx.x] = part * sjd;
 }
 
 // complex64 slots with D >= 2048: the TMA-staged pair-layout matvec of the
@@ -415,6 +446,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
   const KScalars* sc = a.sc + si;
   if (sc->m_eff <= j) return;
   const uint32_t tl = blockIdx.x - rg.x;
+
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const float2* v = basis<float>(s, j);
   const float2* vp = j > 0 ? basis<float>(s, j - 1) : nullptr;
@@ -462,7 +494,9 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
       }
     }
   } else {
-    const float bprev = j > 0 ? static_cast<float>(sc->beta[j - 1]) : 0.f;
+    // w = s_j H basis[j] - beta_{j-1} s_{j-1} basis[j-1] (unnormalised basis, see basis_scale)
+    const float sj = j > 0 ? static_cast<float>(a.lsc[2 * si]) : 1.f;
+    const float bprev = j > 0 ? static_cast<float>(a.lsc[2 * si + 1]) : 0.f;
     const uint32_t pair_part = warp * (64u * kRows) + 2u * lane;
     const float4* v4 = reinterpret_cast<const float4*>(v);
     const float4* vp4 = reinterpret_cast<const float4*>(vp);
@@ -482,10 +516,10 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
         float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (j > 0) pv = vp4[i4];
         float4 o;
-        o.x = fma_(-bprev, pv.x, acc[r][0]);
-        o.y = fma_(-bprev, pv.y, acc[r][1]);
-        o.z = fma_(-bprev, pv.z, acc[r][2]);
-        o.w = fma_(-bprev, pv.w, acc[r][3]);
+        o.x = fma_(-bprev, pv.x, mul_(sj, acc[r][0]));
+        o.y = fma_(-bprev, pv.y, mul_(sj, acc[r][1]));
+        o.z = fma_(-bprev, pv.z, mul_(sj, acc[r][2]));
+        o.w = fma_(-bprev, pv.w, mul_(sj, acc[r][3]));
         w4[i4] = o;
         const float4 vv = v4[i4];
         part += static_cast<double>(vv.x * o.x + vv.y * o.y) + static_cast<double>(vv.z * o.z + vv.w * o.w);
@@ -494,7 +528,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
   }
   part = block_sum(part);
   if (threadIdx.x == 0) {
-    a.partA[blockIdx.x] = part;
+    a.partA[blockIdx.x] = part * (j > 0 ? a.lsc[2 * si] : 1.0);
     if (s_err) atomicExch(a.err, 1);
   }
 }
@@ -509,7 +543,7 @@ __global__ void __launch_bounds__(kBlk) k_b_axpy_norm(BatchArgs a, int j) {
   if (sc->m_eff <= j) return;
   const double al = slot_sum(a.partA, rg);
   if (tl == 0 && threadIdx.x == 0) sc->alpha[j] = al;
-  const Real alr = static_cast<Real>(al);
+  const Real alr = static_cast<Real>(al * basis_scale(sc, j));  // v_j = s_j basis[j]
   const auto* v = basis<Real>(s, j);
   auto* w = basis<Real>(s, j + 1);
   double acc = 0.0;
@@ -522,33 +556,17 @@ __global__ void __launch_bounds__(kBlk) k_b_axpy_norm(BatchArgs a, int j) {
     acc += static_cast<double>(ww.x * ww.x + ww.y * ww.y);
   }
   acc = block_sum(acc);
-  if (threadIdx.x == 0) a.partN[blockIdx.x] = acc;
-}
-
-template <typename Real>
-__global__ void __launch_bounds__(kBlk) k_b_scale_next(BatchArgs a, int j, double brk_rel) {
-  int si, tl;
-  int2 rg;
-  if (!slot_of_block(a, si, tl, rg)) return;
-  const BSlot& s = a.slots[si];
-  KScalars* sc = a.sc + si;
-  if (sc->m_eff <= j) return;
-  const double b = sqrt(slot_sum(a.partN, rg));
-  // breakdown relative to the scale of T (|alpha| and beta so far)
-  double scale = fabs(sc->alpha[j]) + (j > 0 ? sc->beta[j - 1] : 0.0);
-  const bool breakdown = !(b > brk_rel * fmax(scale, 1e-300));
-  if (tl == 0 && threadIdx.x == 0) {
-    sc->beta[j] = b;
-    if (breakdown) sc->m_eff = j + 1;
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    a.partN[blockIdx.x] = acc;
+    __threadfence();  // the partial is visible before this block counts itself done
+    last = atomicAdd(a.slot_cnt + si, 1) == rg.y - 1;
   }
-  if (breakdown) return;
-  const Real inv = static_cast<Real>(1.0 / b);
-  auto* w = basis<Real>(s, j + 1);
-  for (uint32_t m = tl * kBlk + threadIdx.x; m < s.D; m += rg.y * kBlk) {
-    auto ww = w[m];
-    ww.x = mul_(ww.x, inv);
-    ww.y = mul_(ww.y, inv);
-    w[m] = ww;
+  __syncthreads();
+  if (last) {  // every block of the slot has written its partial
+    __threadfence();
+    lanczos_finish_step(a, sc, si, j, rg);
+    if (threadIdx.x == 0) a.slot_cnt[si] = 0;
   }
 }
 
@@ -568,9 +586,9 @@ __global__ void __launch_bounds__(kBlk) k_b_combine(BatchArgs a) {
   const KScalars* sc = a.sc + si;
   __shared__ Real cr[kMaxKrylov], ci[kMaxKrylov];
   const int n = min(sc->m_eff, a.m);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    cr[i] = static_cast<Real>(sc->beta0 * sc->c_re[i]);
-    ci[i] = static_cast<Real>(sc->beta0 * sc->c_im[i]);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {  // v_i = s_i basis[i]
+    cr[i] = static_cast<Real>(sc->beta0 * sc->c_re[i] * basis_scale(sc, i));
+    ci[i] = static_cast<Real>(sc->beta0 * sc->c_im[i] * basis_scale(sc, i));
   }
   __syncthreads();
   auto* y = mvec<Real>(s, s.ev_vec);
@@ -613,6 +631,8 @@ struct Batch {
   int2* d_blk_range = nullptr;
   double* d_part = nullptr;  // 2 x max blocks
   int* d_err = nullptr;      // bounded-wait failure flag
+  int* d_slot_cnt = nullptr;  // per slot: blocks done with axpy_norm (zero between launches)
+  double* d_lsc = nullptr;    // per slot: the next matvec's two Lanczos scalars
   size_t max_blocks = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -624,7 +644,8 @@ struct Batch {
     if (graph) cudaGraphExecDestroy(graph);
     if (stream) cudaStreamDestroy(stream);
     for (void* p : {static_cast<void*>(d_slots), static_cast<void*>(d_sc), static_cast<void*>(d_blk_slot),
-                    static_cast<void*>(d_blk_range), static_cast<void*>(d_part), static_cast<void*>(d_err), arena})
+                    static_cast<void*>(d_blk_range), static_cast<void*>(d_part), static_cast<void*>(d_err),
+                    static_cast<void*>(d_slot_cnt), static_cast<void*>(d_lsc), arena})
       if (p) cudaFree(p);
   }
 
@@ -673,7 +694,9 @@ void capture_tick(Batch& b) {
   a.partA = b.d_part;
   a.partN = b.d_part + b.max_blocks;
   a.err = b.d_err;
-  const double brk = sizeof(Real) == 4 ? 1e-7 : 1e-14;
+  a.brk = sizeof(Real) == 4 ? 1e-7 : 1e-14;
+  a.slot_cnt = b.d_slot_cnt;
+  a.lsc = b.d_lsc;
   if (b.graph) {
     cudaGraphExecDestroy(b.graph);
     b.graph = nullptr;
@@ -691,7 +714,6 @@ void capture_tick(Batch& b) {
     k_b_matvec<Real><<<G, kBlk, 0, b.stream>>>(a, j);
     if (sizeof(Real) == 4) k_b_matvec_c64<kStagesC64><<<G, 32 * (kConsumerWarps + 1), dyn, b.stream>>>(a, j);
     k_b_axpy_norm<Real><<<G, kBlk, 0, b.stream>>>(a, j);
-    k_b_scale_next<Real><<<G, kBlk, 0, b.stream>>>(a, j, brk);
   }
   k_b_tridiag<<<S, 32, 0, b.stream>>>(a);
   k_b_combine<Real><<<G, kBlk, 0, b.stream>>>(a);
@@ -789,6 +811,9 @@ int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylo
     SYK_CUDA(cudaMemset(b.d_blk_range, 0, max_slots * sizeof(int2)));
     SYK_CUDA(cudaMalloc(&b.d_part, 2 * b.max_blocks * sizeof(double)));
     SYK_CUDA(cudaMalloc(&b.d_err, sizeof(int)));
+    SYK_CUDA(cudaMalloc(&b.d_slot_cnt, max_slots * sizeof(int)));
+    SYK_CUDA(cudaMemset(b.d_slot_cnt, 0, max_slots * sizeof(int)));
+    SYK_CUDA(cudaMalloc(&b.d_lsc, 2 * max_slots * sizeof(double)));
     SYK_CUDA(cudaMemset(b.d_err, 0, sizeof(int)));
     SYK_CUDA(cudaMemset(b.d_slots, 0, max_slots * sizeof(syk::BSlot)));
     SYK_CUDA(cudaMemset(b.d_sc, 0, max_slots * sizeof(syk::KScalars)));
