@@ -710,9 +710,19 @@ void capture_tick(Batch& b) {
   k_b_control<Real><<<S, kCtlBlk, 0, b.stream>>>(a);
   k_b_norm<Real><<<G, kBlk, 0, b.stream>>>(a);
   k_b_scale_first<Real><<<G, kBlk, 0, b.stream>>>(a);
+  // complex64 slots of at least one tile take the tiled matvec; the plain one
+  // is captured only when a live slot needs it (the graph is recaptured when
+  // the set of live slots changes).
+  bool plain = sizeof(Real) != 4, tiled = false;
+  for (int s = 0; s < b.max_slots; ++s)
+    if (b.jobs[s].live) {
+      const bool t = sizeof(Real) == 4 && b.jobs[s].job.h->D >= (int64_t(1) << kTileBits);
+      tiled = tiled || t;
+      plain = plain || !t;
+    }
   for (int j = 0; j < b.m; ++j) {
-    k_b_matvec<Real><<<G, kBlk, 0, b.stream>>>(a, j);
-    if (sizeof(Real) == 4) k_b_matvec_c64<kStagesC64><<<G, 32 * (kConsumerWarps + 1), dyn, b.stream>>>(a, j);
+    if (plain) k_b_matvec<Real><<<G, kBlk, 0, b.stream>>>(a, j);
+    if (tiled) k_b_matvec_c64<kStagesC64><<<G, 32 * (kConsumerWarps + 1), dyn, b.stream>>>(a, j);
     k_b_axpy_norm<Real><<<G, kBlk, 0, b.stream>>>(a, j);
   }
   k_b_tridiag<<<S, 32, 0, b.stream>>>(a);
