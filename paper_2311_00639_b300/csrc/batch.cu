@@ -40,6 +40,10 @@ namespace {
 
 constexpr int kBlk = 256;          // threads per block
 constexpr int kCtlBlk = 1024;      // threads of the per-slot control block (its vector stages run on one SM)
+#ifndef SYK_BATCH_GROUPS
+#define SYK_BATCH_GROUPS 2
+#endif
+constexpr int kGroups = SYK_BATCH_GROUPS;  // tick groups (graphs on their own streams)
 constexpr int kMaxBlkPerSlot = 256;  // blocks per slot (partials summed per slot)
 
 enum Stage { S_INIT = 0, S_PART, S_AFTER_U0, S_POINT, S_K1, S_K2, S_K3, S_K4, S_G1, S_G2, S_DONE };
@@ -89,6 +93,8 @@ struct BatchArgs {
   double brk;     // Lanczos breakdown threshold, relative to |alpha_j| + beta_{j-1}
   int* slot_cnt;  // [max slots] blocks of the slot done with k_b_axpy_norm (0 between launches)
   double* lsc;    // [max slots][2] for the next matvec: s_j = 1 / beta_{j-1}, beta_{j-1} s_{j-1}
+  const int* slot_group;  // [max slots] tick group of each live slot (-1: dead)
+  int group;              // the group this tick's graph advances
 };
 
 template <typename Real>
@@ -164,6 +170,7 @@ __device__ __forceinline__ double2 philox_amp(uint64_t g, uint64_t seed, uint64_
 
 template <typename Real>
 __global__ void __launch_bounds__(kCtlBlk) k_b_control(BatchArgs a) {
+  if (a.slot_group[blockIdx.x] != a.group) return;
   BSlot& g = a.slots[blockIdx.x];
   __shared__ BSlot s;
   __shared__ int stop;
@@ -572,6 +579,7 @@ __global__ void __launch_bounds__(kBlk) k_b_axpy_norm(BatchArgs a, int j) {
 
 __global__ void __launch_bounds__(32) k_b_tridiag(BatchArgs a) {
   __shared__ double Z[kMaxKrylov][kMaxKrylov + 1];
+  if (a.slot_group[blockIdx.x] != a.group) return;
   const BSlot& s = a.slots[blockIdx.x];
   if (!s.live || s.done || !s.ev) return;
   tridiag_warp(a.sc + blockIdx.x, a.m, s.z_re, s.z_im, a.tol, Z);
@@ -633,19 +641,31 @@ struct Batch {
   int* d_err = nullptr;      // bounded-wait failure flag
   int* d_slot_cnt = nullptr;  // per slot: blocks done with axpy_norm (zero between launches)
   double* d_lsc = nullptr;    // per slot: the next matvec's two Lanczos scalars
-  size_t max_blocks = 0;
-  cudaStream_t stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  size_t max_blocks = 0;  // per tick group: block map and partials of group g at offset g * max_blocks
+  // Live slots are split into two tick groups, each with its own graph and
+  // stream, so that one group's per-slot serial kernels (tridiagonal step,
+  // control) overlap the other group's Lanczos matvecs.
+  int* d_slot_group = nullptr;
+  std::vector<int> host_group;  // copy of d_slot_group
+  int ngroups = 1;
+  int group_blocks[kGroups] = {};
+  cudaStream_t stream = nullptr;               // group 0; host copies
+  cudaStream_t gstream[kGroups] = {};          // gstream[0] == stream
+  cudaGraphExec_t graph[kGroups] = {};
   bool layout_dirty = true;
   int total_blocks = 0;
   size_t bytes_in_use = 0;
 
   ~Batch() {
-    if (graph) cudaGraphExecDestroy(graph);
+    for (int g = 0; g < kGroups; ++g) {
+      if (graph[g]) cudaGraphExecDestroy(graph[g]);
+      if (g > 0 && gstream[g]) cudaStreamDestroy(gstream[g]);
+    }
     if (stream) cudaStreamDestroy(stream);
     for (void* p : {static_cast<void*>(d_slots), static_cast<void*>(d_sc), static_cast<void*>(d_blk_slot),
                     static_cast<void*>(d_blk_range), static_cast<void*>(d_part), static_cast<void*>(d_err),
-                    static_cast<void*>(d_slot_cnt), static_cast<void*>(d_lsc), arena})
+                    static_cast<void*>(d_slot_cnt), static_cast<void*>(d_lsc), static_cast<void*>(d_slot_group),
+                    arena})
       if (p) cudaFree(p);
   }
 
@@ -683,54 +703,58 @@ struct Batch {
 };
 
 template <typename Real>
-void capture_tick(Batch& b) {
+void capture_tick(Batch& b, int grp) {
   BatchArgs a;
   a.slots = b.d_slots;
   a.sc = b.d_sc;
-  a.blk_slot = b.d_blk_slot;
+  a.blk_slot = b.d_blk_slot + grp * b.max_blocks;
   a.blk_range = b.d_blk_range;
   a.m = b.m;
   a.tol = b.tol;
-  a.partA = b.d_part;
-  a.partN = b.d_part + b.max_blocks;
+  a.partA = b.d_part + 2 * grp * b.max_blocks;
+  a.partN = a.partA + b.max_blocks;
   a.err = b.d_err;
   a.brk = sizeof(Real) == 4 ? 1e-7 : 1e-14;
   a.slot_cnt = b.d_slot_cnt;
   a.lsc = b.d_lsc;
-  if (b.graph) {
-    cudaGraphExecDestroy(b.graph);
-    b.graph = nullptr;
+  a.slot_group = b.d_slot_group;
+  a.group = grp;
+  cudaStream_t st = b.gstream[grp];
+  cudaGraphExec_t& graph = b.graph[grp];
+  if (graph) {
+    cudaGraphExecDestroy(graph);
+    graph = nullptr;
   }
   constexpr size_t dyn = static_cast<size_t>(kStagesC64) * (1u << kTileBits) * 8u;
   if (sizeof(Real) == 4)
     SYK_CUDA(cudaFuncSetAttribute(k_b_matvec_c64<kStagesC64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(dyn)));
-  SYK_CUDA(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
-  const int S = b.max_slots, G = std::max(1, b.total_blocks);
-  k_b_control<Real><<<S, kCtlBlk, 0, b.stream>>>(a);
-  k_b_norm<Real><<<G, kBlk, 0, b.stream>>>(a);
-  k_b_scale_first<Real><<<G, kBlk, 0, b.stream>>>(a);
+  SYK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const int S = b.max_slots, G = std::max(1, b.group_blocks[grp]);
+  k_b_control<Real><<<S, kCtlBlk, 0, st>>>(a);
+  k_b_norm<Real><<<G, kBlk, 0, st>>>(a);
+  k_b_scale_first<Real><<<G, kBlk, 0, st>>>(a);
   // complex64 slots of at least one tile take the tiled matvec; the plain one
   // is captured only when a live slot needs it (the graph is recaptured when
   // the set of live slots changes).
   bool plain = sizeof(Real) != 4, tiled = false;
   for (int s = 0; s < b.max_slots; ++s)
-    if (b.jobs[s].live) {
+    if (b.jobs[s].live && b.host_group[s] == grp) {
       const bool t = sizeof(Real) == 4 && b.jobs[s].job.h->D >= (int64_t(1) << kTileBits);
       tiled = tiled || t;
       plain = plain || !t;
     }
   for (int j = 0; j < b.m; ++j) {
-    if (plain) k_b_matvec<Real><<<G, kBlk, 0, b.stream>>>(a, j);
-    if (tiled) k_b_matvec_c64<kStagesC64><<<G, 32 * (kConsumerWarps + 1), dyn, b.stream>>>(a, j);
-    k_b_axpy_norm<Real><<<G, kBlk, 0, b.stream>>>(a, j);
+    if (plain) k_b_matvec<Real><<<G, kBlk, 0, st>>>(a, j);
+    if (tiled) k_b_matvec_c64<kStagesC64><<<G, 32 * (kConsumerWarps + 1), dyn, st>>>(a, j);
+    k_b_axpy_norm<Real><<<G, kBlk, 0, st>>>(a, j);
   }
-  k_b_tridiag<<<S, 32, 0, b.stream>>>(a);
-  k_b_combine<Real><<<G, kBlk, 0, b.stream>>>(a);
+  k_b_tridiag<<<S, 32, 0, st>>>(a);
+  k_b_combine<Real><<<G, kBlk, 0, st>>>(a);
   cudaGraph_t g;
-  const cudaError_t e = cudaStreamEndCapture(b.stream, &g);
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
   if (e != cudaSuccess) throw Error(SYK_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  const cudaError_t e2 = cudaGraphInstantiate(&b.graph, g, 0);
+  const cudaError_t e2 = cudaGraphInstantiate(&graph, g, 0);
   cudaGraphDestroy(g);
   if (e2 != cudaSuccess) throw Error(SYK_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
 }
@@ -757,32 +781,46 @@ int bguard(const char* fn, F&& f) {
 }
 
 void relayout(syk::Batch& b) {
-  // flattened block -> slot map for live slots; dead slots get no blocks.
-  // Slots are laid out in decreasing term count: a matvec block's work is one
-  // tile times the slot's terms, and the block scheduler starts blocks in
-  // index order, so the heaviest tiles start first and the tail is light.
-  std::vector<int> blk_slot;
-  std::vector<int2> range(b.max_slots, make_int2(0, 0));
+  // Flattened block -> slot maps for live slots, one per tick group; dead
+  // slots get no blocks.  Slots are laid out in decreasing term count: a
+  // matvec block's work is one tile times the slot's terms, and the block
+  // scheduler starts blocks in index order, so the heaviest tiles start first
+  // and the tail is light.  Slots then alternate between the tick groups in
+  // that order (two or more slots per group), which balances their work.
   std::vector<int> order;
   for (int s = 0; s < b.max_slots; ++s)
     if (b.jobs[s].live) order.push_back(s);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return b.jobs[x].job.h->terms.size() > b.jobs[y].job.h->terms.size();
   });
-  for (const int s : order) {
+  b.ngroups = static_cast<int>(std::max<size_t>(1, std::min<size_t>(syk::kGroups, order.size() / 2)));
+  std::vector<int> blk_slot[syk::kGroups];
+  std::vector<int2> range(b.max_slots, make_int2(0, 0));
+  std::vector<int> group(b.max_slots, -1);
+  for (size_t i = 0; i < order.size(); ++i) {
+    const int s = order[i];
+    const int g = static_cast<int>(i % static_cast<size_t>(b.ngroups));
     const int64_t D = b.jobs[s].job.h->D;
     const bool tiles = b.dtype == SYK_C64 && D >= (int64_t(1) << syk::kTileBits);
     const int nb = static_cast<int>(tiles ? std::min<int64_t>(D >> syk::kTileBits, syk::kMaxBlkPerSlot)
                                           : std::min<int64_t>((D + syk::kBlk - 1) / syk::kBlk, syk::kMaxBlkPerSlot));
-    range[s] = make_int2(static_cast<int>(blk_slot.size()), nb);
-    for (int i = 0; i < nb; ++i) blk_slot.push_back(s);
+    range[s] = make_int2(static_cast<int>(blk_slot[g].size()), nb);
+    group[s] = g;
+    for (int k = 0; k < nb; ++k) blk_slot[g].push_back(s);
   }
-  if (blk_slot.empty()) blk_slot.push_back(0);
-  b.total_blocks = static_cast<int>(blk_slot.size());
-  if (static_cast<size_t>(b.total_blocks) > b.max_blocks) throw syk::Error(SYK_EINVAL, "internal: block map overflow");
-  SYK_CUDA(cudaMemcpyAsync(b.d_blk_slot, blk_slot.data(), blk_slot.size() * sizeof(int), cudaMemcpyHostToDevice,
-                           b.stream));
+  for (int g = 0; g < syk::kGroups; ++g) {
+    if (blk_slot[g].empty()) blk_slot[g].push_back(0);
+    b.group_blocks[g] = static_cast<int>(blk_slot[g].size());
+    if (static_cast<size_t>(b.group_blocks[g]) > b.max_blocks)
+      throw syk::Error(SYK_EINVAL, "internal: block map overflow");
+    SYK_CUDA(cudaMemcpyAsync(b.d_blk_slot + g * b.max_blocks, blk_slot[g].data(), blk_slot[g].size() * sizeof(int),
+                             cudaMemcpyHostToDevice, b.stream));
+  }
+  b.total_blocks = 0;
+  for (int g = 0; g < b.ngroups; ++g) b.total_blocks += b.group_blocks[g];
   SYK_CUDA(cudaMemcpyAsync(b.d_blk_range, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice, b.stream));
+  SYK_CUDA(cudaMemcpyAsync(b.d_slot_group, group.data(), group.size() * sizeof(int), cudaMemcpyHostToDevice, b.stream));
+  b.host_group = group;
   SYK_CUDA(cudaStreamSynchronize(b.stream));  // host vectors go out of scope
 }
 }  // namespace
@@ -816,10 +854,12 @@ int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylo
     b.max_blocks = static_cast<size_t>(max_slots) * syk::kMaxBlkPerSlot;
     SYK_CUDA(cudaMalloc(&b.d_slots, max_slots * sizeof(syk::BSlot)));
     SYK_CUDA(cudaMalloc(&b.d_sc, max_slots * sizeof(syk::KScalars)));
-    SYK_CUDA(cudaMalloc(&b.d_blk_slot, b.max_blocks * sizeof(int)));
+    SYK_CUDA(cudaMalloc(&b.d_blk_slot, syk::kGroups * b.max_blocks * sizeof(int)));
+    SYK_CUDA(cudaMalloc(&b.d_slot_group, max_slots * sizeof(int)));
+    SYK_CUDA(cudaMemset(b.d_slot_group, 0xFF, max_slots * sizeof(int)));
     SYK_CUDA(cudaMalloc(&b.d_blk_range, max_slots * sizeof(int2)));
     SYK_CUDA(cudaMemset(b.d_blk_range, 0, max_slots * sizeof(int2)));
-    SYK_CUDA(cudaMalloc(&b.d_part, 2 * b.max_blocks * sizeof(double)));
+    SYK_CUDA(cudaMalloc(&b.d_part, 2 * syk::kGroups * b.max_blocks * sizeof(double)));
     SYK_CUDA(cudaMalloc(&b.d_err, sizeof(int)));
     SYK_CUDA(cudaMalloc(&b.d_slot_cnt, max_slots * sizeof(int)));
     SYK_CUDA(cudaMemset(b.d_slot_cnt, 0, max_slots * sizeof(int)));
@@ -828,6 +868,8 @@ int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylo
     SYK_CUDA(cudaMemset(b.d_slots, 0, max_slots * sizeof(syk::BSlot)));
     SYK_CUDA(cudaMemset(b.d_sc, 0, max_slots * sizeof(syk::KScalars)));
     SYK_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
+    b.gstream[0] = b.stream;
+    for (int g = 1; g < syk::kGroups; ++g) SYK_CUDA(cudaStreamCreateWithFlags(&b.gstream[g], cudaStreamNonBlocking));
     *out = h.release();
   });
 }
@@ -935,17 +977,21 @@ int syk_batch_run(syk_batch_t* h, int max_ticks, int ticks_per_sync, int* n_fini
     if (live == 0) return;
     if (b.layout_dirty) {
       relayout(b);
-      if (b.dtype == SYK_C128)
-        syk::capture_tick<double>(b);
-      else
-        syk::capture_tick<float>(b);
+      for (int g = 0; g < b.ngroups; ++g) {
+        if (b.dtype == SYK_C128)
+          syk::capture_tick<double>(b, g);
+        else
+          syk::capture_tick<float>(b, g);
+      }
       b.layout_dirty = false;
     }
     std::vector<syk::BSlot> dev_slots(b.max_slots);
     for (int done_ticks = 0; done_ticks < max_ticks;) {
       const int n = std::min(ticks_per_sync, max_ticks - done_ticks);
-      for (int i = 0; i < n; ++i) SYK_CUDA(cudaGraphLaunch(b.graph, b.stream));
+      for (int i = 0; i < n; ++i)
+        for (int g = 0; g < b.ngroups; ++g) SYK_CUDA(cudaGraphLaunch(b.graph[g], b.gstream[g]));
       done_ticks += n;
+      for (int g = 1; g < b.ngroups; ++g) SYK_CUDA(cudaStreamSynchronize(b.gstream[g]));
       SYK_CUDA(cudaMemcpyAsync(dev_slots.data(), b.d_slots, b.max_slots * sizeof(syk::BSlot), cudaMemcpyDeviceToHost,
                                b.stream));
       SYK_CUDA(cudaStreamSynchronize(b.stream));
