@@ -294,6 +294,24 @@ def build_lib():
     mod.build()
 
 
+def max_over_ranks(v, dist, device="cuda"):
+    """The maximum of a per-rank float over all ranks (a replica job takes as
+    long as its slowest rank); v itself without a process group."""
+    if dist is None:
+        return v
+    import torch
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def replica_terms(si, N, k, rank):
+    """Replicas only: rank r runs disorder realisation r of the workload."""
+    q, J, _ = si.sample_sparse_syk(N, k, r=rank)
+    return q, J
+
+
 def time_matvecs(h, psi, out, steps, warmup, torch):
     for _ in range(warmup):
         h.apply_H(psi, 0, out=out)
@@ -327,7 +345,7 @@ def ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     barrier = (lambda: dist.barrier()) if dist else (lambda: None)
 
-    q, J, _ = si.sample_sparse_syk(args.N, args.k, r=rank)
+    q, J = replica_terms(si, args.N, args.k, rank)
     h = syk.Terms(args.N, q, J, dtype="c64")
     T, D = h.n_terms, h.D
     psi, _ = h.random_state(seed=1234, state_id=rank, blocks=(0,))
@@ -341,10 +359,7 @@ def ours(args):
     dt = time_matvecs(h, psi, out, args.steps, args.warmup, torch)
     clk = clocks.stop()
     barrier()
-    if dist:
-        tt = torch.tensor([dt], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = tt.item()
+    dt = max_over_ranks(dt, dist)
     per_step = dt / args.steps
     value = world * T * D * args.steps / dt / 1e9
 
@@ -391,7 +406,7 @@ def ours(args):
         t0 = time.perf_counter()
         e2e_steps(ke)
         torch.cuda.synchronize()
-        de = (time.perf_counter() - t0) / ke
+        de = max_over_ranks((time.perf_counter() - t0) / ke, dist)
         e2e = {"value": world * T * D / de / 1e9, "unit": UNIT, "h2d_bytes_per_step": D * 8,
                "d2h_bytes_per_step": D * 8, "ms_per_step": de * 1e3, "steps": ke,
                "pipeline": "3 streams, 2 device buffer sets: upload i+1 and download i overlap H psi i"}
@@ -407,7 +422,7 @@ def ours(args):
         psi64, _ = h64.random_state(seed=1234, state_id=rank, blocks=(0,))
         out64 = h64.empty()
         k64 = max(1, min(3, args.steps))
-        d64 = time_matvecs(h64, psi64, out64, k64, min(args.warmup, 2), torch)
+        d64 = max_over_ranks(time_matvecs(h64, psi64, out64, k64, min(args.warmup, 2), torch), dist)
         fp64 = {"value": world * T * D * k64 / d64 / 1e9, "unit": UNIT, "ms_per_step": d64 * 1e3 / k64,
                 "dtype": "c128 (f64)"}
         del psi64, out64
