@@ -44,7 +44,9 @@ struct MV {
   const KScalars* sc;
   int j;
   unsigned long long* sched = nullptr;  // complex64 EPI_STORE: [0] next item, [1] CTAs finished
-  uint32_t ny = 1;                      // complex64 EPI_STORE: states in this launch
+  uint32_t ny = 1;                      // complex64 EPI_STORE: states in this launch (chunks when split)
+  const typename CT<Real>::T* prev = nullptr;  // complex64 split pass: the partial sum of earlier passes
+  int chunk_terms = 0;                         // complex64 split pass: terms per chunk
 };
 
 // Epilogue shared by the first Lanczos pass and the second (regenerating)
@@ -356,8 +358,16 @@ __global__ void __launch_bounds__(256) k_matvec_tma(MV<Real> p, int* err_flag) {
 // first job completes, which orders it for the consumers; an item >= n_items
 // ends the CTA's stream.  Every wait is bounded (1 s); on a timeout the CTA
 // records the error, stops issuing, drains its copies and exits.
-template <int EPI, bool ACCUM, int S>
+//
+// SPLIT (EPI_STORE only; passes of a small block with many terms, one state):
+// the items are (chunk, tile) pairs; item (c, tile) applies terms
+// [t0 + c chunk_terms, ...) of the pass to the tile and writes its partial sum
+// to p.out + c D (a workspace); chunk 0 also carries the earlier passes' sum
+// (p.prev).  k_sum_chunks then adds the chunks in order, so the result does not
+// depend on which CTA ran which chunk.
+template <int EPI, bool ACCUM, int S, bool SPLIT = false>
 __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_matvec_c64(MV<float> p, int* err_flag) {
+  static_assert(!SPLIT || EPI == EPI_STORE, "split passes only store their sum");
   constexpr uint32_t kTileBytes = (1u << kTileBits) * 8u;
   constexpr bool kQueue = EPI == EPI_STORE;
   constexpr int kRing = 8;  // items in flight between producer and consumers: at most S + 1
@@ -423,18 +433,23 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[stg])) : "memory");
           break;
         }
-        const uint64_t soff = (ybase + (item >> tshift)) * p.D;
+        const uint64_t hi = item >> tshift;  // state, or chunk when SPLIT
+        const uint64_t soff = SPLIT ? 0ull : (ybase + hi) * p.D;
+        const int ct0 = SPLIT ? t0 + static_cast<int>(hi) * p.chunk_terms : t0;
+        const int ct1 = SPLIT ? min(t1, ct0 + p.chunk_terms) : t1;
+        const bool acc_i = ACCUM && (!SPLIT || hi == 0);
         const uint32_t tb = tile_base(item);
-        for (int tt = ACCUM ? t0 - 1 : t0; tt < t1 && !*(volatile int*)&s_err; ++tt) {
-          const bool phi = ACCUM && tt < t0;
+        for (int tt = acc_i ? ct0 - 1 : ct0; tt < ct1 && !*(volatile int*)&s_err; ++tt) {
+          const bool phi = acc_i && tt < ct0;
           const uint2 xf = phi ? make_uint2(0u, 0u) : make_uint2(__ldg(&p.rec[tt].x), __ldg(&p.rec[tt].flags));
-          if (!phi && !(xf.y & kTermRunStart)) continue;  // the run's tile is already staged
+          if (!phi && !(xf.y & kTermRunStart) && !(SPLIT && tt == ct0)) continue;  // the run's tile is staged
           const uint32_t stg = static_cast<uint32_t>(q % S);
           if (q >= S && !mbar_wait_bounded(smem_u32(&empty_bar[stg]), static_cast<uint32_t>(((q / S) - 1) & 1),
                                            &s_err))
             break;
-          if (tt == (ACCUM ? t0 - 1 : t0)) s_item[k % kRing] = item;
-          const float2* src = phi ? p.out + soff + tb : p.psi + soff + (tb ^ (xf.x & ~((1u << kTileBits) - 1u)));
+          if (tt == (acc_i ? ct0 - 1 : ct0)) s_item[k % kRing] = item;
+          const float2* src = phi ? (SPLIT ? p.prev : p.out) + soff + tb
+                                  : p.psi + soff + (tb ^ (xf.x & ~((1u << kTileBits) - 1u)));
           const uint32_t bar = smem_u32(&full_bar[stg]);
           mbar_expect_tx(bar, kTileBytes);
           bulk_g2s_hint(smem0 + stg * kTileBytes, src, kTileBytes, bar, (phi || (xf.y & kTermStraggler)) ? stream : keep);
@@ -482,15 +497,19 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
         item = static_item(k);
       }
       if (item >= n_items) break;
-      const uint64_t soff = (ybase + (item >> tshift)) * p.D;
-      const float4* psi4 = reinterpret_cast<const float4*>(p.psi + soff);
+      const uint64_t hi = item >> tshift;  // state, or chunk when SPLIT
+      const uint64_t soff = (ybase + hi) * p.D;
+      const int ct0 = SPLIT ? t0 + static_cast<int>(hi) * p.chunk_terms : t0;
+      const int ct1 = SPLIT ? min(t1, ct0 + p.chunk_terms) : t1;
+      const bool acc_i = ACCUM && (!SPLIT || hi == 0);
+      const float4* psi4 = reinterpret_cast<const float4*>(p.psi + (SPLIT ? 0ull : soff));
       float4* out4 = reinterpret_cast<float4*>(p.out + soff);
       const uint32_t mt = tile_base(item) + pair_part;  // amplitude of row 0, even
-      if (Tp > 0) d = __ldg(reinterpret_cast<const uint4*>(p.rec + t0));  // the tile's first term
+      if (Tp > 0) d = __ldg(reinterpret_cast<const uint4*>(p.rec + ct0));  // the tile's first term
       // The sum starts from the partial sum of the earlier passes (ACCUM: the
       // producer's first job of the tile is this tile of `out`), else from 0.
       float a[kRows][4];
-      if (ACCUM) {
+      if (acc_i) {
         const uint32_t stg = ring.stg;
         const bool ok = mbar_wait_bounded(smem_u32(&full_bar[stg]), ring.ph, &s_err);
         const float4* t4 = reinterpret_cast<const float4*>(smem_raw + stg * kTileBytes);
@@ -510,7 +529,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
 #pragma unroll
         for (int r = 0; r < kRows; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
       }
-      c64_terms<S>(t0, t1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_terms<S, SPLIT>(ct0, ct1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
         const uint32_t i4 = (mt >> 1) + 32u * r;
@@ -965,8 +984,55 @@ void launch_pass(const syk_terms* h, const Shape& s, const MV<Real>& q, unsigned
   }
 }
 
+// out = sum over chunks c = 0..C-1 of ws[c] (in that order), float4 at a time.
+__global__ void k_sum_chunks(const float4* __restrict__ ws, int C, uint64_t n4, float4* __restrict__ out) {
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    float4 a = ws[i];
+    for (int c = 1; c < C; ++c) {
+      const float4 v = ws[static_cast<uint64_t>(c) * n4 + i];
+      a.x += v.x;
+      a.y += v.y;
+      a.z += v.z;
+      a.w += v.w;
+    }
+    out[i] = a;
+  }
+}
+
+// A split complex64 pass: chunks of terms on different CTAs into the
+// workspace, then their sum into q.out (which, for passes after the first,
+// chunk 0 started from).
+template <bool ACCUM>
+void launch_split_pass(const syk_terms* h, int ip, const MV<float>& q, cudaStream_t st) {
+  constexpr size_t dyn = static_cast<size_t>(kStagesC64) * (1u << kTileBits) * 8u;
+  static std::atomic<uint64_t> configured{0};
+  const uint64_t bit = 1ull << (h->device & 63);
+  if (!(configured.load() & bit)) {
+    SYK_CUDA(cudaFuncSetAttribute(k_matvec_c64<EPI_STORE, ACCUM, kStagesC64, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn)));
+    configured.fetch_or(bit);
+  }
+  const int C = h->split_chunks[ip];
+  MV<float> qs = q;
+  qs.out = h->d_split_ws;
+  qs.prev = q.out;
+  qs.ny = static_cast<uint32_t>(C);
+  qs.chunk_terms = h->split_terms[ip];
+  qs.sched = h->d_sched;
+  const uint64_t items = (static_cast<uint64_t>(h->D) >> kTileBits) * C;
+  const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(items, static_cast<uint64_t>(h->n_sm) * kC64CtasPerSm));
+  k_matvec_c64<EPI_STORE, ACCUM, kStagesC64, true><<<grid, 32 * (kConsumerWarps + 1), dyn, st>>>(qs, h->d_err);
+  const uint64_t n4 = static_cast<uint64_t>(h->D) / 2;
+  const unsigned g2 = static_cast<unsigned>(std::min<uint64_t>((n4 + 255) / 256, static_cast<uint64_t>(h->n_sm) * 8));
+  k_sum_chunks<<<g2, 256, 0, st>>>(reinterpret_cast<const float4*>(h->d_split_ws), C, n4,
+                                   reinterpret_cast<float4*>(q.out));
+}
+
 // One launch per pass: passes before the last write (first) or accumulate
-// plain partial sums; the last pass applies the requested epilogue.
+// plain partial sums; the last pass applies the requested epilogue.  A split
+// complex64 pass (plan_split) stores its sum like the others; when it is the
+// last pass, the epilogue then runs as an accumulating pass with no terms.
 template <typename Real, int EPI>
 void run_matvec(const syk_terms* h, const MV<Real>& p, int64_t nstates, cudaStream_t st) {
   const Shape s = shape_of(h);
@@ -985,6 +1051,16 @@ void run_matvec(const syk_terms* h, const MV<Real>& p, int64_t nstates, cudaStre
     for (int ip = 0; ip < np; ++ip) {
       q.pass = h->d_passes + ip;
       const bool last = ip == np - 1, accum = ip > 0;
+      if constexpr (std::is_same<Real, float>::value) {
+        if (s.R == 8 && gy == 1 && h->split_chunks[ip] > 1) {
+          accum ? launch_split_pass<true>(h, ip, q, st) : launch_split_pass<false>(h, ip, q, st);
+          if (last && EPI != EPI_STORE) {
+            q.pass = h->d_pass_tail;
+            launch_pass<Real, EPI, true>(h, s, q, gy, st);
+          }
+          continue;
+        }
+      }
       if (!last)
         accum ? launch_pass<Real, EPI_STORE, true>(h, s, q, gy, st)
               : launch_pass<Real, EPI_STORE, false>(h, s, q, gy, st);
@@ -1004,6 +1080,33 @@ void dispatch(int dtype, F&& f) {
 }
 
 }  // namespace
+
+// Split a complex64 pass into chunks of terms when its block has too few tiles
+// to fill the GPU and the pass has many terms (dense SYK, small N with large
+// k): chunks x tiles ~ the resident CTAs, at least 32 terms a chunk.  The
+// workspace holds one partial sum per chunk: at most (CTAs + tiles) tiles.
+void plan_split(syk_terms* h) {
+  const size_t np = h->passes.size();
+  h->split_chunks.assign(np, 1);
+  h->split_terms.assign(np, 0);
+  h->split_ws_bytes = 0;
+  if (h->dtype != SYK_C64 || h->D < (int64_t(1) << kTileBits)) return;
+  const int64_t ntiles = h->D >> kTileBits;
+  const int64_t cap = static_cast<int64_t>(h->n_sm) * kC64CtasPerSm;
+  if (2 * ntiles > cap) return;
+  int64_t cmax = 1;
+  for (size_t p = 0; p < np; ++p) {
+    const int64_t Tp = h->passes[p].t1 - h->passes[p].t0;
+    int64_t C = std::min<int64_t>((cap + ntiles - 1) / ntiles, Tp / 32);
+    if (C < 2) continue;
+    const int64_t Tc = (Tp + C - 1) / C;
+    C = (Tp + Tc - 1) / Tc;  // every chunk non-empty
+    h->split_chunks[p] = static_cast<int>(C);
+    h->split_terms[p] = static_cast<int>(Tc);
+    cmax = std::max(cmax, C);
+  }
+  if (cmax > 1) h->split_ws_bytes = static_cast<size_t>(cmax) * static_cast<size_t>(h->D) * 8u;
+}
 
 int vec_grid(const syk_terms* h) {
   const uint64_t need = (static_cast<uint64_t>(h->D) + 255) / 256;

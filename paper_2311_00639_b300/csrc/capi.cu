@@ -90,7 +90,10 @@ void upload_table(syk_terms* h) {
     const size_t n = h->terms.size();
     const size_t rb = h->dtype == SYK_C128 ? 8 : 4;
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-    const size_t pass_bytes = up(h->passes.size() * sizeof(syk::PassPlan));
+    syk::plan_split(h);
+    // the passes, then one more: the last pass's tile order with no terms, run
+    // for the epilogue after a split last pass
+    const size_t pass_bytes = up((h->passes.size() + 1) * sizeof(syk::PassPlan));
     const size_t rec_bytes = up((n + 1) * sizeof(syk::TermF));  // + one zero record: prefetch past the end
     const size_t zi_bytes = up(std::max<size_t>(n, 1) * 4);
     const size_t bytes = 2 * up(std::max<size_t>(n, 1) * 4) + 2 * up(std::max<size_t>(n, 1) * rb) + pass_bytes + 256 +
@@ -103,6 +106,12 @@ void upload_table(syk_terms* h) {
     char* hc1 = hc0 + up(std::max<size_t>(n, 1) * rb);
     char* hp = hc1 + up(std::max<size_t>(n, 1) * rb);
     std::memcpy(hp, h->passes.data(), h->passes.size() * sizeof(syk::PassPlan));
+    if (!h->passes.empty()) {
+      syk::PassPlan tail = h->passes.back();
+      tail.t0 = tail.ti = tail.t1;
+      for (int c = 0; c < 9; ++c) tail.cls[c] = tail.t1;
+      std::memcpy(hp + h->passes.size() * sizeof(syk::PassPlan), &tail, sizeof(tail));
+    }
     char* hr0 = hp + pass_bytes + 256;
     char* hr1 = hr0 + rec_bytes;
     uint32_t* hzi = reinterpret_cast<uint32_t*>(hr1 + rec_bytes);
@@ -168,6 +177,15 @@ void upload_table(syk_terms* h) {
     h->d_coef[0] = d + (hc0 - p);
     h->d_coef[1] = d + (hc1 - p);
     h->d_passes = reinterpret_cast<syk::PassPlan*>(d + (hp - p));
+    h->d_pass_tail = h->d_passes + h->passes.size();
+    if (h->d_split_ws) {
+      cudaFree(h->d_split_ws);
+      h->d_split_ws = nullptr;
+    }
+    if (h->split_ws_bytes && cudaMalloc(&h->d_split_ws, h->split_ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw syk::Error(SYK_ENOMEM, "device allocation of the split-pass workspace failed");
+    }
     h->d_err = reinterpret_cast<int*>(d + (hp - p) + pass_bytes);  // zeroed with the host image
     h->d_sched = reinterpret_cast<unsigned long long*>(d + (hp - p) + pass_bytes + 64);  // likewise
     h->d_termf[0] = reinterpret_cast<syk::TermF*>(d + (hr0 - p));

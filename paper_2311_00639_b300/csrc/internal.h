@@ -86,6 +86,8 @@ constexpr int kTermBodyShift = 8;
 inline uint32_t term_body(uint32_t x, uint32_t z, bool imag) {
   return (imag ? 32u : 0u) | ((x & 1u) << 4) | ((z & 1u) << 3) | ((x >> 6) & 7u);
 }
+// Chooses the term split of each complex64 pass (apply.cu).
+void plan_split(syk_terms* h);
 // Reorders `terms` by pass and returns the passes.
 std::vector<PassPlan> plan_passes(std::vector<BlockString>& terms, int L, size_t elem_bytes, size_t l2_budget,
                                    double hbm_ratio);
@@ -125,11 +127,19 @@ struct syk_terms {
   unsigned long long* d_sched = nullptr;  // complex64 matvec tile counter pair (zero between launches)
   uint32_t* d_zi = nullptr;  // z | (imag << 31) per term (batched engine)
   int64_t n_runs = 0;  // complex64 record runs (input tiles staged per output tile, all passes)
+  // complex64 passes of a small block with many terms are split into chunks of
+  // terms applied by different CTAs (plan_split): chunks per pass (1 = not
+  // split) and terms per chunk; partial sums go to d_split_ws.
+  std::vector<int> split_chunks, split_terms;
+  float2* d_split_ws = nullptr;
+  size_t split_ws_bytes = 0;
+  syk::PassPlan* d_pass_tail = nullptr;  // the last pass's tile order with no terms (epilogue after a split)
   int n_sm = 148;
   syk_terms() = default;
   syk_terms(const syk_terms&) = delete;
   syk_terms& operator=(const syk_terms&) = delete;
   ~syk_terms() {
     if (d_mem) cudaFree(d_mem);
+    if (d_split_ws) cudaFree(d_split_ws);
   }
 };

@@ -174,7 +174,9 @@ struct StageRing {
 #define SYK_C64_BODY8(k) \
   SYK_C64_BODY(k) SYK_C64_BODY(k + 1) SYK_C64_BODY(k + 2) SYK_C64_BODY(k + 3) SYK_C64_BODY(k + 4) \
   SYK_C64_BODY(k + 5) SYK_C64_BODY(k + 6) SYK_C64_BODY(k + 7)
-template <int S>
+// FORCE: [tb0, tb1) is a chunk of a pass whose ends need not be run ends; the
+// chunk's first term starts a run and its last ends one.
+template <int S, bool FORCE = false>
 __device__ __forceinline__ void c64_terms(int tb0, int tb1, uint4& d, StageRing<S>& ring, float (&a)[kRows][4],
                                           const TermF* __restrict__ rec, uint32_t mt, uint32_t pair_part,
                                           const unsigned char* smem, uint64_t* full_bar, uint64_t* empty_bar,
@@ -185,7 +187,9 @@ __device__ __forceinline__ void c64_terms(int tb0, int tb1, uint4& d, StageRing<
   for (int tt = tb0; tt < tb1; ++tt) {
     const uint4 cur = d;
     d = __ldg(reinterpret_cast<const uint4*>(rec + tt + 1));
-    const uint32_t x = cur.x, z = cur.y, cb = cur.z, fl = cur.w;
+    const uint32_t x = cur.x, z = cur.y, cb = cur.z;
+    uint32_t fl = cur.w;
+    if (FORCE) fl |= (tt == tb0 ? kTermRunStart : 0u) | (tt == tb1 - 1 ? kTermRunEnd : 0u);
     if (fl & kTermRunStart) {
       ok = mbar_wait_bounded(smem_u32(&full_bar[ring.stg]), ring.ph, s_err);
       t4 = reinterpret_cast<const float4*>(smem + ring.stg * (1u << kTileBits) * 8u);

@@ -223,6 +223,30 @@ def test_krylov_c64_plans_agree_N44(syk):
         assert h.device_error() == 0
 
 
+def test_dense_syk_split_passes_N24(syk):
+    """Dense SYK at N=24 (10626 terms, one 2048-amplitude tile): the complex64
+    pass is split into chunks of terms on different CTAs and summed in order.
+    H psi on sampled rows against the definition; a Krylov step (its last pass
+    split, the Lanczos epilogue applied by a pass with no terms) against the
+    complex128 path, which does not split."""
+    t = torch()
+    N = 24
+    q, J, _ = si.sample_dense_syk(N, 0)
+    with syk.Terms(N, q, J, dtype="c64") as h, syk.Terms(N, q, J, dtype="c128") as h2:
+        D = h.D
+        psi = h.random_state(seed=5, state_id=0, blocks=(0,))[0]
+        out = h.apply_H(psi, 0).cpu().numpy()
+        rows = np.arange(0, D, 7, dtype=np.uint64)[:300]
+        ref = ham.rows_of_Hpsi(N, q, J, "jw", 0, rows, lambda b, m: si.philox_state(N, 5, 0, np.uint64(b * D) + m))
+        assert rel_err(out[rows.astype(np.int64)], ref) < 2e-5
+        x = psi / t.linalg.vector_norm(psi)
+        y64, st = h.krylov_evolve(x, 0, 0.1, 0.5, tol=1e-7)
+        y128, _ = h2.krylov_evolve(x.to(t.complex128), 0, 0.1, 0.5, tol=1e-12)
+        assert st.matvecs > 0
+        assert (t.max(t.abs(y64.to(t.complex128) - y128)) / t.max(t.abs(y128))).item() < 2e-5
+        assert h.device_error() == 0
+
+
 # ------------------------------------------------------------ random state --
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_random_state_matches_counter_definition(syk, dtype):
