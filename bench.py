@@ -58,6 +58,8 @@ def parse():
                          "m+1 vectors (m=10 stored: 64 s/point; m=20 two-pass: 80 s/point; m=8 stored: 100 s/point)")
     ap.add_argument("--batch-realizations", type=int, default=32)
     ap.add_argument("--batch-states", type=int, default=4)
+    ap.add_argument("--batch-slots", type=int, default=4096,
+                    help="batch slots (jobs live at once; the rest wait for admission)")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-tmax", type=float, default=20.0)
     ap.add_argument("--serve-dt", type=float, default=1.0)
@@ -215,7 +217,7 @@ def otoc_batched(args, syk, si, torch, rank=0):
         q, J, _ = si.sample_sparse_syk(N, k, seed=700_000 + 1000 * rank + r)
         reals.append((N, q, J, syk.Terms(N, q, J, dtype="c64")))
     jobs = [(r, s) for r in range(R) for s in range(S)]
-    b = syk.Batch(dtype="c64", max_slots=len(jobs), max_bytes=40 << 30, m=30)
+    b = syk.Batch(dtype="c64", max_slots=min(len(jobs), args.batch_slots), max_bytes=40 << 30, m=30)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     results = {}
