@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-tmax", type=float, default=20.0)
     ap.add_argument("--serve-dt", type=float, default=1.0)
+    ap.add_argument("--serve-load", type=float, default=0.75,
+                    help="Poisson arrival rate as a fraction of the closed-loop capacity (all requests at t=0)")
     return ap.parse_args()
 
 
@@ -274,7 +276,7 @@ def otoc_served(args, syk, torch):
     res = srv.run(cap_reqs)
     cap = len(res) / (time.perf_counter() - t0)
     srv.close()
-    rate = 0.75 * cap
+    rate = args.serve_load * cap
     reqs = serve.served_workload(n, rate=rate, seed=12, **kw)
     srv = serve.OtocServer(dtype="c64", max_slots=256, hbm_budget_bytes=100 << 30, ticks_per_step=8)
     t0 = time.perf_counter()
@@ -282,7 +284,7 @@ def otoc_served(args, syk, torch):
     wall = time.perf_counter() - t0
     srv.close()
     summ = serve.summarize(res, wall)
-    summ.update({"arrival_rate_per_s": rate, "closed_loop_capacity_per_s": cap,
+    summ.update({"arrival_rate_per_s": rate, "closed_loop_capacity_per_s": cap, "load": args.serve_load,
                  "workload": f"{n} Poisson requests, N 28..48 (P ~ 0.7^((N-28)/2)), k 0.5..4, beta 2..20, "
                              f"t 0..{args.serve_tmax:g} step {args.serve_dt:g}, c64, HBM budget 100 GB"})
     return summ
