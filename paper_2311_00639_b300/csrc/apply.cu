@@ -1,13 +1,17 @@
-// Device kernels of the sparse-SYK hot path.
-//
-//  * k_matvec      — H_P psi, the matrix-free Pauli-string action of
-//                    Algorithm 1 (supplement Sec. I.A), with optional fused
-//                    Lanczos epilogues;
+// Device kernels of the sparse-SYK hot path.  H_P psi is the matrix-free
+// Pauli-string action of Algorithm 1 (supplement Sec. I.A), with optional
+// fused Lanczos epilogues, in four forms by vector size and type:
+//  * k_matvec_c64  — complex64, >= 2048 amplitudes: warp-specialised TMA
+//                    pipeline over L2-blocked passes (the benchmark kernel);
+//  * k_matvec_tma  — complex128, >= 2048 amplitudes: TMA-staged tiles;
+//  * k_matvec      — fewer than 2048 amplitudes: coalesced gathers (below);
+//  * k_matvec_tiny — fewer than 32 amplitudes;
+//  * k_sum_chunks  — the in-order sum of a split pass's chunks;
 //  * k_chi         — one Majorana between parity blocks;
 //  * k_random      — Philox4x32-10 + Box-Muller typical-state amplitudes;
 //  * vector kernels for the Lanczos recurrence and the OTOC inner products.
 //
-// Matvec layout.  A warp owns 32*R consecutive output amplitudes
+// k_matvec layout.  A warp owns 32*R consecutive output amplitudes
 // m = base + 32 r + lane (r < R).  For a term (x, z, c) the input of lane
 // `lane` in row r is psi[(row ^ x_hi) | (lane ^ x_lo)] with x_lo = x & 31,
 // so every load instruction of the warp reads one contiguous, aligned
@@ -331,15 +335,17 @@ __global__ void __launch_bounds__(256) k_matvec_tma(MV<Real> p, int* err_flag) {
 // complex64 matvec, warp-specialised TMA pipeline (vectors of >= 2048 amplitudes).
 //
 // Warp kConsumerWarps is the producer: its lane 0 streams input tiles (one
-// 16 KiB bulk copy per (tile, term) job) into S shared-memory stages, waiting
+// 16 KiB bulk copy per (tile, run) job) into S shared-memory stages, waiting
 // on an "empty" mbarrier per stage before reusing it.  Warps 0..kConsumerWarps-1
 // consume: each lane owns two neighbouring amplitudes in kRows rows of its
 // warp's slice (m = tile + 64 kRows w + 64 r + 2 lane + {0, 1}), reads both
 // inputs of a term with one 16-byte shared load, and signals the stage free
-// with one arrive per warp.  Terms of a pass are sorted by class
-// (imag, x & 1, z & 1) so that the pair swap (x & 1) and the sign difference
-// inside the pair (z & 1) are compile-time; the row permutation (bits 6-8 of
-// x) is a warp-uniform switch.
+// with one arrive per warp.  Inside a pass the records are ordered by input
+// tile (x >> 11), then class; consecutive terms with the same input tile (a
+// run) share one staged copy.  A term's class (imag, x & 1, z & 1: the pair
+// swap and the sign difference inside the pair) and its row permutation
+// (x bits 6-8), precomputed in the record, select one of 64 compile-time
+// bodies (c64_terms).
 //
 // Tile order.  The work items of a launch are (state, tile) pairs in the
 // pass's super-tile order.  Passes that only store their sum (EPI_STORE) start
@@ -420,7 +426,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
       const uint64_t stream = l2_policy_evict_first();  // the output tile: read once per pass
       uint64_t q = 0, issued = 0;
       uint64_t next = static_item(0);  // the first item is blockIdx.x in both orders
-      // Job stream per tile: [the tile of `out` (ACCUM only)] then one input tile per term.
+      // Job stream per tile: [the tile of `out` (ACCUM only)] then one input tile per run.
       for (uint64_t k = 0; !*(volatile int*)&s_err; ++k) {
         const uint64_t item = next < n_items ? next : kEnd;
         if (item != kEnd) next = queue ? gridDim.x + atomicAdd(p.sched, 1ull) : static_item(k + 1);
@@ -915,13 +921,7 @@ struct Shape {
   int R, warps, grid;  // R == 8: TMA-staged 2048-amplitude tiles
 };
 
-constexpr int kStagesF = 4;  // complex64: 4 x 16 KiB in flight per CTA
-constexpr int kStagesD = 3;  // complex128: 3 x 32 KiB
-
-template <typename Real>
-constexpr int stages() {
-  return sizeof(Real) == 4 ? kStagesF : kStagesD;
-}
+constexpr int kStagesD = 3;  // complex128 k_matvec_tma: 3 x 32 KiB in flight per CTA
 
 Shape shape_of(const syk_terms* h) {
   Shape s;
@@ -969,16 +969,18 @@ void launch_pass(const syk_terms* h, const Shape& s, const MV<Real>& q, unsigned
     }
   }
   if (s.R == 8) {
-    constexpr int S = stages<Real>();
-    constexpr size_t dyn = TmaSmem<Real, S>::kDynBytes;
-    static std::atomic<uint64_t> configured{0};  // one bit per device ordinal (< 64)
-    const uint64_t bit = 1ull << (h->device & 63);
-    if (!(configured.load() & bit)) {
-      SYK_CUDA(cudaFuncSetAttribute(k_matvec_tma<Real, EPI, ACCUM, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(dyn)));
-      configured.fetch_or(bit);
+    if constexpr (std::is_same<Real, double>::value) {  // complex64 took k_matvec_c64 above
+      constexpr int S = kStagesD;
+      constexpr size_t dyn = TmaSmem<Real, S>::kDynBytes;
+      static std::atomic<uint64_t> configured{0};  // one bit per device ordinal (< 64)
+      const uint64_t bit = 1ull << (h->device & 63);
+      if (!(configured.load() & bit)) {
+        SYK_CUDA(cudaFuncSetAttribute(k_matvec_tma<Real, EPI, ACCUM, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(dyn)));
+        configured.fetch_or(bit);
+      }
+      k_matvec_tma<Real, EPI, ACCUM, S><<<dim3(s.grid, gy), 256, dyn, st>>>(q, h->d_err);
     }
-    k_matvec_tma<Real, EPI, ACCUM, S><<<dim3(s.grid, gy), 256, dyn, st>>>(q, h->d_err);
   } else {
     k_matvec<Real, 1, EPI, ACCUM><<<dim3(s.grid, gy), 32 * s.warps, 0, st>>>(q);
   }

@@ -13,7 +13,7 @@
 namespace syk {
 
 constexpr int kMaxKrylov = 64;   // largest Krylov dimension per substep
-constexpr int kTileBits = 11;    // amplitudes per matvec block tile = 2^11 (8 warps x 8 rows x 32 lanes)
+constexpr int kTileBits = 11;    // amplitudes per matvec tile = 2^11 (one 16 KiB complex64 bulk copy)
 constexpr int kMaxPartials = 2048;  // per-state reduction partials (>= any grid.x)
 
 struct Error : std::runtime_error {
