@@ -649,6 +649,7 @@ struct Batch {
   std::vector<int> host_group;  // copy of d_slot_group
   int ngroups = 1;
   int group_blocks[kGroups] = {};
+  double group_cost[kGroups] = {};  // sum of T x D over the group's live slots (work per tick)
   cudaStream_t stream = nullptr;               // group 0; host copies
   cudaStream_t gstream[kGroups] = {};          // gstream[0] == stream
   cudaGraphExec_t graph[kGroups] = {};
@@ -782,30 +783,52 @@ int bguard(const char* fn, F&& f) {
 
 void relayout(syk::Batch& b) {
   // Flattened block -> slot maps for live slots, one per tick group; dead
-  // slots get no blocks.  Slots are laid out in decreasing term count: a
-  // matvec block's work is one tile times the slot's terms, and the block
-  // scheduler starts blocks in index order, so the heaviest tiles start first
-  // and the tail is light.  Slots then alternate between the tick groups in
-  // that order (two or more slots per group), which balances their work.
+  // slots get no blocks.  Groups by work (terms x amplitudes of a slot): the
+  // heaviest slots, up to half of the total work, form group 0 and the rest
+  // group 1, and the run loop gives each group ticks in inverse proportion to
+  // its work per tick, so light slots are not held to the pace of the heavy
+  // ones (and both groups finish a sync period together).  Inside a group the
+  // slots are laid out in decreasing term count: a matvec block's work is one
+  // tile times the slot's terms, and the block scheduler starts blocks in
+  // index order, so the heaviest tiles start first and the tail is light.
   std::vector<int> order;
   for (int s = 0; s < b.max_slots; ++s)
     if (b.jobs[s].live) order.push_back(s);
+  auto work = [&](int s) {
+    return static_cast<double>(b.jobs[s].job.h->terms.size()) * static_cast<double>(b.jobs[s].job.h->D);
+  };
+  std::vector<int> group(b.max_slots, -1);
+  b.ngroups = static_cast<int>(std::max<size_t>(1, std::min<size_t>(syk::kGroups, order.size() / 2)));
+  for (auto& c : b.group_cost) c = 0.0;
+  {
+    std::vector<int> by_work = order;
+    std::stable_sort(by_work.begin(), by_work.end(), [&](int x, int y) { return work(x) > work(y); });
+    double total = 0.0;
+    for (const int s : by_work) total += work(s);
+    double acc = 0.0;
+    for (size_t i = 0; i < by_work.size(); ++i) {
+      const int s = by_work[i];
+      // group 0 takes slots while it holds less than half the work (at least
+      // one slot, and at least one slot is left for group 1)
+      const bool heavy = b.ngroups == 1 || i == 0 || (acc < 0.5 * total && i + 1 < by_work.size());
+      const int g = heavy ? 0 : 1;
+      if (heavy) acc += work(s);
+      group[s] = g;
+      b.group_cost[g] += work(s);
+    }
+  }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return b.jobs[x].job.h->terms.size() > b.jobs[y].job.h->terms.size();
   });
-  b.ngroups = static_cast<int>(std::max<size_t>(1, std::min<size_t>(syk::kGroups, order.size() / 2)));
   std::vector<int> blk_slot[syk::kGroups];
   std::vector<int2> range(b.max_slots, make_int2(0, 0));
-  std::vector<int> group(b.max_slots, -1);
-  for (size_t i = 0; i < order.size(); ++i) {
-    const int s = order[i];
-    const int g = static_cast<int>(i % static_cast<size_t>(b.ngroups));
+  for (const int s : order) {
+    const int g = group[s];
     const int64_t D = b.jobs[s].job.h->D;
     const bool tiles = b.dtype == SYK_C64 && D >= (int64_t(1) << syk::kTileBits);
     const int nb = static_cast<int>(tiles ? std::min<int64_t>(D >> syk::kTileBits, syk::kMaxBlkPerSlot)
                                           : std::min<int64_t>((D + syk::kBlk - 1) / syk::kBlk, syk::kMaxBlkPerSlot));
     range[s] = make_int2(static_cast<int>(blk_slot[g].size()), nb);
-    group[s] = g;
     for (int k = 0; k < nb; ++k) blk_slot[g].push_back(s);
   }
   for (int g = 0; g < syk::kGroups; ++g) {
@@ -988,8 +1011,20 @@ int syk_batch_run(syk_batch_t* h, int max_ticks, int ticks_per_sync, int* n_fini
     std::vector<syk::BSlot> dev_slots(b.max_slots);
     for (int done_ticks = 0; done_ticks < max_ticks;) {
       const int n = std::min(ticks_per_sync, max_ticks - done_ticks);
-      for (int i = 0; i < n; ++i)
-        for (int g = 0; g < b.ngroups; ++g) SYK_CUDA(cudaGraphLaunch(b.graph[g], b.gstream[g]));
+      // n ticks for the heaviest group; lighter groups get proportionally more
+      // (at most 16 n), so a sync period takes about as long on every stream
+      int ng[syk::kGroups] = {};
+      double cmax = 0.0;
+      for (int g = 0; g < b.ngroups; ++g) cmax = std::max(cmax, b.group_cost[g]);
+      int most = n;
+      for (int g = 0; g < b.ngroups; ++g) {
+        const double r = b.group_cost[g] > 0.0 ? cmax / b.group_cost[g] : 1.0;
+        ng[g] = static_cast<int>(std::min<double>(16.0 * n, std::max<double>(n, std::floor(n * r))));
+        most = std::max(most, ng[g]);
+      }
+      for (int i = 0; i < most; ++i)
+        for (int g = 0; g < b.ngroups; ++g)
+          if (i < ng[g]) SYK_CUDA(cudaGraphLaunch(b.graph[g], b.gstream[g]));
       done_ticks += n;
       for (int g = 1; g < b.ngroups; ++g) SYK_CUDA(cudaStreamSynchronize(b.gstream[g]));
       SYK_CUDA(cudaMemcpyAsync(dev_slots.data(), b.d_slots, b.max_slots * sizeof(syk::BSlot), cudaMemcpyDeviceToHost,
