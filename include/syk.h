@@ -27,10 +27,12 @@
  *     16-byte aligned.  Every call with a cudaStream_t is asynchronous on that
  *     stream unless stated otherwise.
  *   * A complex64 handle keeps a device tile counter that its H psi passes
- *     draw work from; calls that apply one handle (syk_apply_H,
- *     syk_krylov_evolve[_noalloc], syk_otoc) must therefore not overlap on
- *     the GPU: issue them on one stream, or order the streams with events.
- *     Different handles are independent.
+ *     draw work from and, for blocks of at most ~2^19 amplitudes with many
+ *     terms, a workspace for the partial sums of passes split across CTAs;
+ *     calls that apply one handle (syk_apply_H, syk_krylov_evolve[_noalloc],
+ *     syk_otoc) must therefore not overlap on the GPU: issue them on one
+ *     stream, or order the streams with events.  Different handles are
+ *     independent.
  *   * Return value: SYK_OK (0) or a negative status.  syk_last_error() gives
  *     the message of the last failing call on the calling thread.  No C++
  *     exception crosses this interface.
