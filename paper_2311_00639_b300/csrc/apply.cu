@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_ma
             break;
           if (tt == (acc_i ? ct0 - 1 : ct0)) s_item[k % kRing] = item;
           const float2* src = phi ? (SPLIT ? p.prev : p.out) + soff + tb
-                                  : p.psi + soff + (tb ^ (xf.x & ~((1u << kTileBits) - 1u)));
+                                  : p.psi + soff + (tb ^ (xf.x & kTermXMask & ~((1u << kTileBits) - 1u)));
           const uint32_t bar = smem_u32(&full_bar[stg]);
           mbar_expect_tx(bar, kTileBytes);
           bulk_g2s_hint(smem0 + stg * kTileBytes, src, kTileBytes, bar, (phi || (xf.y & kTermStraggler)) ? stream : keep);

@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
           if (!(xf.y & kTermRunStart)) continue;  // the run's tile is already staged
           const uint32_t stg = q % S;
           if (q >= S && !mbar_wait_bounded(smem_u32(&empty_bar[stg]), ((q / S) - 1) & 1u, &s_err)) break;
-          const float2* src = v + (tb ^ (xf.x & ~((1u << kTileBits) - 1u)));
+          const float2* src = v + (tb ^ (xf.x & kTermXMask & ~((1u << kTileBits) - 1u)));
           const uint32_t bar = smem_u32(&full_bar[stg]);
           mbar_expect_tx(bar, kTileBytes);
           bulk_g2s_hint(smem0 + stg * kTileBytes, src, kTileBytes, bar, keep);

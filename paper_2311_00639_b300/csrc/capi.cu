@@ -138,12 +138,12 @@ void upload_table(syk_terms* h) {
       h->n_runs += start ? 1 : 0;
       for (int b = 0; b < 2; ++b) {
         syk::TermF r;
-        r.x = t.x;
-        r.z = t.z;
+        r.x = t.x | (((t.z >> 7) & 1u) << 31);  // z bit 7 (row sign pattern, see TermF)
+        r.z = t.z | (((t.z >> 8) & 1u) << 31);  // z bit 8
         r.c = static_cast<float>(t.coef[b]);
         r.flags = (t.straggler ? syk::kTermStraggler : 0u) | (start ? syk::kTermRunStart : 0u) |
                   (end ? syk::kTermRunEnd : 0u) | (t.imag ? syk::kTermImag : 0u) |
-                  (syk::term_body(t.x, t.z, t.imag) << syk::kTermBodyShift);
+                  (syk::term_body(t.x, t.z, t.imag) << syk::kTermBodyShift) | (((t.z >> 6) & 1u) << 31);
         std::memcpy((b ? hr1 : hr0) + k * sizeof(syk::TermF), &r, sizeof(r));
       }
     }

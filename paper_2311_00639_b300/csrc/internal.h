@@ -82,6 +82,11 @@ constexpr uint32_t kTermRunEnd = 4u;     // last term of a run: its stage is rel
 constexpr uint32_t kTermImag = 8u;       // coefficient i * c
 // Bits 8-13 of flags: the consumer body of the term, 32 imag + 16 (x & 1) +
 // 8 (z & 1) + ((x >> 6) & 7) (class and row permutation of the 8-row layout).
+// Bit 31 of flags, x and z (x and z use at most 31 bits) hold z's bits 6, 7
+// and 8: the sign pattern of the 8 rows, so that the consumer forms each
+// row's signed coefficient with one masked XOR.  Readers of x for addresses
+// use kTermXMask.
+constexpr uint32_t kTermXMask = 0x7FFFFFFFu;
 constexpr int kTermBodyShift = 8;
 inline uint32_t term_body(uint32_t x, uint32_t z, bool imag) {
   return (imag ? 32u : 0u) | ((x & 1u) << 4) | ((z & 1u) << 3) | ((x >> 6) & 7u);

@@ -197,13 +197,22 @@ __device__ __forceinline__ void c64_terms(int tb0, int tb1, uint4& d, StageRing<
     if (ok) {
       // sign (-1)^{popc(z & m)} of row r: the lane/warp/tile part popc(z & mt)
       // and the row part popc(z & 64 r) = parity of (z >> 6) & r, folded into
-      // the coefficient's sign bit.
+      // the coefficient's sign bit.  z's bits 6, 7, 8 sit in bit 31 of fl, x
+      // and z (TermF); mt < 2^31, so bit 31 of z does not reach the popc.
+      constexpr uint32_t M = 0x80000000u;
       const uint32_t s0 = (__popc(z & mt) << 31) ^ cb;
-      const uint32_t p0 = (z << 25) & 0x80000000u, p1 = (z << 24) & 0x80000000u, p2 = (z << 23) & 0x80000000u;
       float c[kRows];
-#pragma unroll
-      for (int r = 0; r < kRows; ++r)
-        c[r] = __uint_as_float(s0 ^ ((r & 1) ? p0 : 0u) ^ ((r & 2) ? p1 : 0u) ^ ((r & 4) ? p2 : 0u));
+      {
+        const uint32_t c1 = s0 ^ (fl & M), c2 = s0 ^ (x & M), c3 = c1 ^ (x & M);
+        c[0] = __uint_as_float(s0);
+        c[1] = __uint_as_float(c1);
+        c[2] = __uint_as_float(c2);
+        c[3] = __uint_as_float(c3);
+        c[4] = __uint_as_float(s0 ^ (z & M));
+        c[5] = __uint_as_float(c1 ^ (z & M));
+        c[6] = __uint_as_float(c2 ^ (z & M));
+        c[7] = __uint_as_float(c3 ^ (z & M));
+      }
       const uint32_t pa2 = (pair_part ^ (x & kPairXMask)) >> 1;  // float4 index of the row-0 input pair
       switch ((fl >> kTermBodyShift) & 63u) {
         SYK_C64_BODY8(0)
