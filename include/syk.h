@@ -301,6 +301,16 @@ int syk_batch_info(const syk_batch_t* batch, int* live_jobs, size_t* bytes_in_us
 /* Device bytes a job needs (0 on bad arguments). */
 size_t syk_batch_job_bytes(const syk_batch_t* batch, const syk_terms_t* h, int n_t);
 
+/*
+ * syk_bounded_wait_selftest — failure-detection self-test (no paper
+ * counterpart): one CTA waits, with the bounded wait of the TMA pipelines, on
+ * an mbarrier that nothing completes.  Returns SYK_ETIMEOUT after the wait
+ * limit (~1 s) — the expected outcome — with the context still usable;
+ * SYK_ECUDA if the wait did not expire or a CUDA call failed.  Synchronises
+ * `stream`.
+ */
+int syk_bounded_wait_selftest(syk_stream_t stream);
+
 /* Message of the last failing call on this thread (always NUL-terminated). */
 int syk_last_error(char* buf, size_t n);
 /* Library version string. */

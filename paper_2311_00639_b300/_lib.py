@@ -63,6 +63,7 @@ SIGNATURES = {
     "syk_batch_run": (_I, [_P, _I, _I, C.POINTER(_I), _P, _I]),
     "syk_batch_info": (_I, [_P, C.POINTER(_I), C.POINTER(_SZ), C.POINTER(_SZ)]),
     "syk_batch_job_bytes": (_SZ, [_P, _P, _I]),
+    "syk_bounded_wait_selftest": (_I, [_P]),
     "syk_last_error": (_I, [C.c_char_p, _SZ]),
     "syk_version": (C.c_char_p, []),
 }

@@ -45,6 +45,12 @@ def _host_arrays(quads, J):
     return q, j
 
 
+def bounded_wait_selftest(stream=None) -> int:
+    """Status of syk_bounded_wait_selftest: SYK_ETIMEOUT (-4) when the bounded
+    device wait expired as intended (the failure path, without a fault)."""
+    return int(L.load().syk_bounded_wait_selftest(_stream(stream)))
+
+
 def compile_terms_host(N: int, quads, J, rep: str = "jw") -> dict:
     """Host-only term compilation (no GPU): x, z, coef_U, coef_D, imag arrays."""
     lib = L.load()
