@@ -4,7 +4,7 @@
 // F = F_U + F_D (Eq. (2) of the main text evaluated on a typical state, or
 // summed over all basis states for the exact trace).
 //
-// Per state and block P the driver keeps four vectors of the block:
+// Per state and block P the host loop keeps four vectors of the block:
 //   u0  = e^{-b H/8} psi_P                  (computed once),
 //   bra = e^{-(it_n + b/8) H} psi_P          (advanced by e^{-i dt H} per grid point),
 //   k1, k2: the ket chain, rebuilt for every t (it depends on t in all four evolutions).
