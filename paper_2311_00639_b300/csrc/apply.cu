@@ -923,12 +923,19 @@ struct Shape {
 
 constexpr int kStagesD = 3;  // complex128 k_matvec_tma: 3 x 32 KiB in flight per CTA
 
+// complex128 blocks of fewer tiles than this take the amplitude-parallel
+// gather kernel: the TMA kernel runs one CTA per tile, so a small block would
+// leave most SMs idle (B300, OTOC curves of the paper's benchmark rows: N=30,
+// k=3 639 -> 260 ms; dense N=30 126 -> 15 s; N=40 1.41 -> 1.30 s).
+constexpr uint64_t kC128GatherTiles = 512;
+
 Shape shape_of(const syk_terms* h) {
   Shape s;
   const uint64_t D = static_cast<uint64_t>(h->D);
   if (D < 32) return {0, 1, 1};
   const uint64_t ntiles_cap = static_cast<uint64_t>(h->n_sm);
-  if (D >= (1ull << kTileBits)) {
+  const bool c128_gather = h->dtype == SYK_C128 && (D >> kTileBits) < kC128GatherTiles;
+  if (D >= (1ull << kTileBits) && !c128_gather) {
     s.R = 8;
     s.warps = 8;
     // CTAs resident per SM given the stage buffers.
