@@ -173,7 +173,7 @@ int syk_random_state(const syk_terms_t* h, uint64_t seed, uint64_t state_id, voi
 
 /* Krylov (Lanczos) propagation parameters.  Zero fields take the defaults. */
 typedef struct {
-  int m;            /* Krylov dimension per substep (default 30, max 64) */
+  int m;            /* Krylov dimension per substep (default 20 C64, 30 C128; max 64) */
   double tol;       /* relative error target per evolve (default 1e-12 C128, 1e-6 C64) */
   int max_substeps; /* default 1000 */
   int reorth;       /* 1: full re-orthogonalisation (classical Gram-Schmidt twice) */

@@ -83,7 +83,9 @@ class KrylovStats:
         return f"KrylovStats(matvecs={self.matvecs}, substeps={self.substeps}, err_est={self.err_est:.3g})"
 
 
-def _params(m=30, tol=None, max_substeps=0, reorth=False, two_pass=False):
+def _params(m=0, tol=None, max_substeps=0, reorth=False, two_pass=False):
+    """syk_krylov_params; zero fields take the library's defaults (m: 20 for
+    complex64, 30 for complex128)."""
     return L.KrylovParams(int(m), float(tol or 0.0), int(max_substeps), int(bool(reorth)), int(bool(two_pass)))
 
 

@@ -71,7 +71,7 @@ struct Params {
 
 Params resolve(const syk_terms* h, const syk_krylov_params* p) {
   Params r;
-  r.m = (p && p->m) ? p->m : 30;
+  r.m = (p && p->m) ? p->m : syk::default_krylov_m(h->dtype);
   r.tol = (p && p->tol > 0) ? p->tol : (h->dtype == SYK_C128 ? 1e-12 : 1e-6);
   r.max_sub = (p && p->max_substeps) ? p->max_substeps : 1000;
   r.reorth = p && p->reorth;

@@ -103,6 +103,10 @@ std::vector<PassPlan> plan_passes(std::vector<BlockString>& terms, int L, size_t
 // they keep small super-tiles.
 inline size_t default_l2_budget(int dtype) { return dtype == SYK_C64 ? size_t(32) << 20 : size_t(2) << 20; }
 inline double default_hbm_ratio(int dtype) { return dtype == SYK_C64 ? 3.0 : 1.5; }
+// Default Krylov dimension per substep: the fastest OTOC curves on B300
+// (complex64, N=30: m=20 176 ms, m=30 227 ms; complex128 at its 1e-12
+// tolerance: m=30 260 ms, m=20 291 ms).
+inline int default_krylov_m(int dtype) { return dtype == SYK_C64 ? 20 : 30; }
 
 // Device view of a compiled term table, in compute precision Real.
 template <typename Real>

@@ -71,7 +71,7 @@ extern "C" int syk_krylov_evolve_noalloc(const syk_terms_t* h, int block, double
     SYK_REQUIRE(x && y, "null x or y");
     SYK_REQUIRE(((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0,
                 "x and y must be 16-byte aligned");
-    const int m = (p && p->m) ? p->m : 30;
+    const int m = (p && p->m) ? p->m : syk::default_krylov_m(h->dtype);
     const double tol = (p && p->tol > 0) ? p->tol : (h->dtype == SYK_C128 ? 1e-12 : 1e-6);
     const int max_sub = (p && p->max_substeps) ? p->max_substeps : 1000;
     const bool reorth = p && p->reorth, two_pass = p && p->two_pass;
