@@ -219,7 +219,8 @@ def otoc_batched(args, syk, si, torch, rank=0):
         q, J, _ = si.sample_sparse_syk(N, k, seed=700_000 + 1000 * rank + r)
         reals.append((N, q, J, syk.Terms(N, q, J, dtype="c64")))
     jobs = [(r, s) for r in range(R) for s in range(S)]
-    b = syk.Batch(dtype="c64", max_slots=min(len(jobs), args.batch_slots), max_bytes=40 << 30, m=30)
+    # Krylov dimension: the library default for complex64 (20; 30 measured 14% slower here)
+    b = syk.Batch(dtype="c64", max_slots=min(len(jobs), args.batch_slots), max_bytes=40 << 30)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     results = {}

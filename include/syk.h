@@ -284,7 +284,9 @@ typedef struct {
                                 e^{-iHt} chi_a e^{-bH/2} |psi> (supplement, Green function; b unused) */
 } syk_otoc_job;
 enum { SYK_JOB_OTOC = 0, SYK_JOB_GREEN = 1 };
-/* max_bytes: device arena for job state (allocated once); max_slots: jobs in flight. */
+/* max_bytes: device arena for job state (allocated once); max_slots: jobs in flight;
+ * p: Krylov parameters shared by all jobs (zero fields take the defaults of
+ * syk_krylov_params; two_pass and reorth must be 0). */
 int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylov_params* p, syk_batch_t** out);
 int syk_batch_destroy(syk_batch_t* batch);
 /* Admit a job; SYK_EAGAIN if no slot or no arena range is free (retry after a run). */

@@ -302,7 +302,7 @@ class Batch:
     dicts {tag, F (complex [n_t]), otoc (normalised), matvecs, substeps, status}.
     """
 
-    def __init__(self, dtype: str = "c64", max_slots: int = 64, max_bytes: int = 1 << 30, m: int = 30, tol=None):
+    def __init__(self, dtype: str = "c64", max_slots: int = 64, max_bytes: int = 1 << 30, m: int = 0, tol=None):
         self._lib = L.load()
         h = C.c_void_p()
         p = _params(m=m, tol=tol)

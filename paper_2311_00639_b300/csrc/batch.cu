@@ -875,7 +875,7 @@ int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylo
     syk::Batch& b = h->b;
     b.dtype = dtype;
     b.max_slots = max_slots;
-    b.m = (p && p->m) ? p->m : 30;
+    b.m = (p && p->m) ? p->m : syk::default_krylov_m(dtype);  // complex64 batch: 20 beat 30 by 14% on B300
     b.tol = (p && p->tol > 0) ? p->tol : (dtype == SYK_C128 ? 1e-12 : 1e-6);
     SYK_REQUIRE(b.m >= 2 && b.m <= syk::kMaxKrylov, "Krylov dimension m must be in [2, 64]");
     SYK_REQUIRE(!(p && (p->two_pass || p->reorth)), "the batch engine stores the basis (no two_pass / reorth)");
