@@ -177,7 +177,7 @@ def reference_arm(args):
 
 # sources whose change invalidates the committed DRAM-traffic capture: the
 # kernel, its shared helpers, the pass planner and the record layout
-KERNEL_SOURCES = ("apply.cu", "tma_common.cuh", "device_common.cuh", "plan.cpp", "capi.cu", "internal.h")
+KERNEL_SOURCES = ("apply.cu", "tma_common.cuh", "device_common.cuh", "plan.cpp", "records.cpp", "capi.cu", "internal.h")
 
 
 def measured_traffic(T, D):

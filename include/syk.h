@@ -134,6 +134,50 @@ int syk_terms_export(const syk_terms_t* h, uint32_t* x, uint32_t* z, double* coe
 int syk_compile_terms_host(int N, int64_t T, const int32_t* quads, const double* J, int rep, int64_t capacity,
                            int64_t* n_terms, uint32_t* x, uint32_t* z, double* coef_U, double* coef_D,
                            uint8_t* imag);
+/* One matvec pass of a host plan (syk_plan_host). */
+typedef struct {
+  int32_t t0, ti, t1;   /* terms [t0, t1) of the plan order: [t0, ti) real, [ti, t1) imaginary */
+  uint32_t emask;       /* amplitude-index bits that the pass's covered terms do not flip; the
+                           pass visits one value of them (a super-tile) at a time */
+  int32_t cls[9];       /* terms of class c = 4 imag + 2 (x & 1) + (z & 1) are [cls[c], cls[c+1]) */
+  int32_t split_chunks; /* complex64: CTAs that share each output tile (1 = not split) */
+  int32_t split_terms;  /* terms per chunk of a split pass (0 if not split) */
+  uint32_t dep[3][256]; /* visit order: the pass's b-th tile starts at amplitude
+                           dep[0][b & 255] | dep[1][(b >> 8) & 255] | dep[2][(b >> 16) & 255] */
+} syk_pass_info;
+
+/* Outputs of syk_plan_host.  The caller sets the capacities and array
+ * pointers (HOST memory; any pointer may be NULL); the call sets the counts.
+ * Arrays are written only when both capacities cover the counts, so a first
+ * call with zero capacities queries the sizes. */
+typedef struct {
+  int64_t term_capacity, pass_capacity;
+  syk_pass_info* passes; /* [pass_capacity] */
+  uint32_t* x;           /* [term_capacity], plan order (pass, class, x, z) */
+  uint32_t* z;
+  double* coef_U;
+  double* coef_D;
+  uint8_t* imag;
+  uint8_t* straggler; /* 1: the term reads outside its pass's super-tile (from HBM) */
+  uint32_t* records;  /* [2][n_terms + 1][4]: the complex64 records of block U, then D, as the
+                         kernel reads them: x, z, coefficient (float bits), flags */
+  int64_t n_terms, n_passes;
+  int64_t n_runs; /* records that start a run (a new staged input tile) */
+} syk_plan_host_out;
+
+/*
+ * Host-only (no CUDA call): the pass plan and complex64 record layout that
+ * syk_build_terms followed by syk_terms_replan(l2_budget_bytes,
+ * straggler_ratio) sets up for these terms, on a device with n_sm SMs.
+ * Same argument rules as syk_build_terms and syk_terms_replan.  Records
+ * within a pass are ordered by (x >> 11, class, x, z); flags bit 0
+ * straggler, 1 run start, 2 run end, 3 imaginary coefficient, bits 8-13 the
+ * consumer body 32 imag + 16 (x & 1) + 8 (z & 1) + ((x >> 6) & 7); bit 31 of
+ * flags, x and z hold bits 6, 7 and 8 of z (x and z fit in 31 bits).
+ * Errors: SYK_EINVAL.
+ */
+int syk_plan_host(int N, int64_t T, const int32_t* quads, const double* J, int dtype, int rep,
+                  size_t l2_budget_bytes, double straggler_ratio, int n_sm, syk_plan_host_out* out);
 /*
  * Host-only: chi_n from block P as (chi psi)[m] = c_P (-1)^{popc(z & m)} psi[m ^ x]
  * in the other block; c_P = re[P] + i im[P] (arrays of 2).

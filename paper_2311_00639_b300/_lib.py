@@ -36,6 +36,19 @@ class OtocJob(C.Structure):
                 ("basis_index", C.c_int64), ("kind", C.c_int)]
 
 
+class PassInfo(C.Structure):
+    _fields_ = [("t0", C.c_int32), ("ti", C.c_int32), ("t1", C.c_int32), ("emask", C.c_uint32),
+                ("cls", C.c_int32 * 9), ("split_chunks", C.c_int32), ("split_terms", C.c_int32),
+                ("dep", (C.c_uint32 * 256) * 3)]
+
+
+class PlanHostOut(C.Structure):
+    _fields_ = [("term_capacity", C.c_int64), ("pass_capacity", C.c_int64), ("passes", C.c_void_p),
+                ("x", C.c_void_p), ("z", C.c_void_p), ("coef_U", C.c_void_p), ("coef_D", C.c_void_p),
+                ("imag", C.c_void_p), ("straggler", C.c_void_p), ("records", C.c_void_p),
+                ("n_terms", C.c_int64), ("n_passes", C.c_int64), ("n_runs", C.c_int64)]
+
+
 # name -> (restype, argtypes); every symbol include/syk.h declares.
 _P = C.c_void_p
 _I, _I64, _U64, _D, _SZ = C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_size_t
@@ -47,6 +60,7 @@ SIGNATURES = {
     "syk_terms_export": (_I, [_P, _P, _P, _P, _P, _P]),
     "syk_compile_terms_host": (_I, [_I, _I64, _P, _P, _I, _I64, C.POINTER(_I64), _P, _P, _P, _P, _P]),
     "syk_compile_chi_host": (_I, [_I, _I, _I, _P, _P, _P, _P]),
+    "syk_plan_host": (_I, [_I, _I64, _P, _P, _I, _I, _SZ, _D, _I, C.POINTER(PlanHostOut)]),
     "syk_apply_H": (_I, [_P, _I, _P, _P, _I64, _P]),
     "syk_apply_chi": (_I, [_P, _I, _I, _P, _P, _I64, _P]),
     "syk_random_state": (_I, [_P, _U64, _U64, _P, _P, _P]),

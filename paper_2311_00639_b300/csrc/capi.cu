@@ -107,46 +107,17 @@ void upload_table(syk_terms* h) {
     char* hp = hc1 + up(std::max<size_t>(n, 1) * rb);
     std::memcpy(hp, h->passes.data(), h->passes.size() * sizeof(syk::PassPlan));
     if (!h->passes.empty()) {
-      syk::PassPlan tail = h->passes.back();
-      tail.t0 = tail.ti = tail.t1;
-      for (int c = 0; c < 9; ++c) tail.cls[c] = tail.t1;
+      const syk::PassPlan tail = syk::tail_pass(h->passes.back());
       std::memcpy(hp + h->passes.size() * sizeof(syk::PassPlan), &tail, sizeof(tail));
     }
     char* hr0 = hp + pass_bytes + 256;
     char* hr1 = hr0 + rec_bytes;
     uint32_t* hzi = reinterpret_cast<uint32_t*>(hr1 + rec_bytes);
     for (size_t i = 0; i < n; ++i) hzi[i] = h->terms[i].z | (h->terms[i].imag ? 0x80000000u : 0u);
-    // complex64 records: within each pass, terms that read the same input
-    // tile (equal x >> kTileBits) are made adjacent and flagged as a run.
-    std::vector<size_t> rec_order(n);
-    std::iota(rec_order.begin(), rec_order.end(), size_t(0));
-    auto rec_key = [&](size_t i) {
-      const auto& t = h->terms[i];
-      return std::make_tuple(t.x >> syk::kTileBits, 4 * int(t.imag) + 2 * int(t.x & 1u) + int(t.z & 1u), t.x, t.z);
-    };
-    for (const auto& ps : h->passes)
-      std::stable_sort(rec_order.begin() + ps.t0, rec_order.begin() + ps.t1,
-                       [&](size_t a, size_t b) { return rec_key(a) < rec_key(b); });
-    std::vector<char> pass_end(n + 1, 0);
-    for (const auto& ps : h->passes) pass_end[ps.t1] = 1;
-    h->n_runs = 0;
-    for (size_t k = 0; k < n; ++k) {
-      const auto& t = h->terms[rec_order[k]];
-      const uint32_t hi = t.x >> syk::kTileBits;
-      const bool start = k == 0 || pass_end[k] || (h->terms[rec_order[k - 1]].x >> syk::kTileBits) != hi;
-      const bool end = k + 1 == n || pass_end[k + 1] || (h->terms[rec_order[k + 1]].x >> syk::kTileBits) != hi;
-      h->n_runs += start ? 1 : 0;
-      for (int b = 0; b < 2; ++b) {
-        syk::TermF r;
-        r.x = t.x | (((t.z >> 7) & 1u) << 31);  // z bit 7 (row sign pattern, see TermF)
-        r.z = t.z | (((t.z >> 8) & 1u) << 31);  // z bit 8
-        r.c = static_cast<float>(t.coef[b]);
-        r.flags = (t.straggler ? syk::kTermStraggler : 0u) | (start ? syk::kTermRunStart : 0u) |
-                  (end ? syk::kTermRunEnd : 0u) | (t.imag ? syk::kTermImag : 0u) |
-                  (syk::term_body(t.x, t.z, t.imag) << syk::kTermBodyShift) | (((t.z >> 6) & 1u) << 31);
-        std::memcpy((b ? hr1 : hr0) + k * sizeof(syk::TermF), &r, sizeof(r));
-      }
-    }
+    std::vector<syk::TermF> rec[2];
+    h->n_runs = syk::build_records(h->terms, h->passes, rec);
+    std::memcpy(hr0, rec[0].data(), (n + 1) * sizeof(syk::TermF));
+    std::memcpy(hr1, rec[1].data(), (n + 1) * sizeof(syk::TermF));
     for (size_t i = 0; i < n; ++i) {
       hx[i] = h->terms[i].x;
       hz[i] = h->terms[i].z;
@@ -313,6 +284,66 @@ int syk_compile_terms_host(int N, int64_t T, const int32_t* quads, const double*
       if (cD) cD[i] = terms[i].coef[1];
       if (imag) imag[i] = terms[i].imag ? 1 : 0;
     }
+  });
+}
+
+int syk_plan_host(int N, int64_t T, const int32_t* quads, const double* J, int dtype, int rep,
+                  size_t l2_budget_bytes, double straggler_ratio, int n_sm, syk_plan_host_out* out) {
+  return guarded("syk_plan_host", [&] {
+    SYK_REQUIRE(out != nullptr, "null output");
+    SYK_REQUIRE(N >= 4 && N <= 64 && N % 2 == 0, "N must be even and in [4, 64]");
+    SYK_REQUIRE(T >= 0 && T <= (int64_t(1) << 31) - 1, "T out of range");
+    SYK_REQUIRE(T == 0 || (quads && J), "null quads or J");
+    SYK_REQUIRE(dtype == SYK_C64 || dtype == SYK_C128, "dtype must be SYK_C64 or SYK_C128");
+    SYK_REQUIRE(rep == SYK_REP_JW || rep == SYK_REP_PAPER, "rep must be SYK_REP_JW or SYK_REP_PAPER");
+    SYK_REQUIRE(l2_budget_bytes == 0 || l2_budget_bytes >= 4096, "l2_budget_bytes must be 0 or >= 4096");
+    SYK_REQUIRE(std::isfinite(straggler_ratio) && straggler_ratio >= 0, "straggler_ratio must be >= 0");
+    SYK_REQUIRE(n_sm >= 1, "n_sm must be >= 1");
+    SYK_REQUIRE(out->term_capacity >= 0 && out->pass_capacity >= 0, "negative capacity");
+    if (l2_budget_bytes == 0) {
+      l2_budget_bytes = syk::default_l2_budget(dtype);
+      straggler_ratio = syk::default_hbm_ratio(dtype);
+    }
+    syk_terms h;  // host fields only: nothing is allocated on a device
+    h.N = N;
+    h.L = N / 2 - 1;
+    h.D = int64_t(1) << h.L;
+    h.dtype = dtype;
+    h.rep = rep;
+    h.n_sm = n_sm;
+    syk::compile_terms(N, rep, T, quads, J, h.terms, h.n_real, h.n_xgroups);
+    h.passes = syk::plan_passes(h.terms, h.L, syk::elem_bytes(dtype), l2_budget_bytes, straggler_ratio);
+    syk::plan_split(&h);
+    std::vector<syk::TermF> rec[2];
+    const size_t n = h.terms.size();
+    out->n_runs = syk::build_records(h.terms, h.passes, rec);
+    out->n_terms = static_cast<int64_t>(n);
+    out->n_passes = static_cast<int64_t>(h.passes.size());
+    if (out->term_capacity < out->n_terms || out->pass_capacity < out->n_passes) return;
+    for (size_t p = 0; p < h.passes.size() && out->passes; ++p) {
+      const syk::PassPlan& ps = h.passes[p];
+      syk_pass_info& o = out->passes[p];
+      o.t0 = ps.t0;
+      o.ti = ps.ti;
+      o.t1 = ps.t1;
+      o.emask = ps.emask;
+      for (int c = 0; c < 9; ++c) o.cls[c] = ps.cls[c];
+      o.split_chunks = h.split_chunks[p];
+      o.split_terms = h.split_terms[p];
+      std::memcpy(o.dep, ps.dep, sizeof(o.dep));
+    }
+    for (size_t i = 0; i < n; ++i) {
+      const auto& t = h.terms[i];
+      if (out->x) out->x[i] = t.x;
+      if (out->z) out->z[i] = t.z;
+      if (out->coef_U) out->coef_U[i] = t.coef[0];
+      if (out->coef_D) out->coef_D[i] = t.coef[1];
+      if (out->imag) out->imag[i] = t.imag ? 1 : 0;
+      if (out->straggler) out->straggler[i] = t.straggler ? 1 : 0;
+    }
+    if (out->records)
+      for (int b = 0; b < 2; ++b)
+        std::memcpy(out->records + static_cast<size_t>(b) * (n + 1) * 4, rec[b].data(), (n + 1) * sizeof(syk::TermF));
   });
 }
 

@@ -93,6 +93,12 @@ inline uint32_t term_body(uint32_t x, uint32_t z, bool imag) {
 }
 // Chooses the term split of each complex64 pass (apply.cu).
 void plan_split(syk_terms* h);
+// Complex64 records of both blocks in the kernel's order, n + 1 per block (the
+// last one zero); returns the number of runs (records.cpp).
+int64_t build_records(const std::vector<BlockString>& terms, const std::vector<PassPlan>& passes,
+                      std::vector<TermF> rec[2]);
+// The last pass's tile order with no terms (the epilogue after a split pass).
+PassPlan tail_pass(const PassPlan& last);
 // Reorders `terms` by pass and returns the passes.
 std::vector<PassPlan> plan_passes(std::vector<BlockString>& terms, int L, size_t elem_bytes, size_t l2_budget,
                                    double hbm_ratio);
