@@ -19,7 +19,11 @@ paper (arXiv 2311.00639) for obviousness, not speed:
 * ``dynamics``    exact e^{-zH} by eigendecomposition and by
                   scipy's expm_multiply;
 * ``otoc``        the regularised OTOC of Eq. (2) as an exact trace and as a
-                  single-state expectation (full space and parity blocks).
+                  single-state expectation (full space and parity blocks);
+* ``spin``        Pauli-string (spin-chain) Hamiltonians of the paper's
+                  outlook: dense Kronecker products, basis-state maps, CSR
+                  and sampled rows; their OTOC is ``otoc`` with W, V given
+                  as matrices.
 
 Conventions (shared as a written spec with the CUDA side, not as code):
   qubit s <-> bit s of the basis index; operators are Kronecker products
@@ -33,6 +37,6 @@ Conventions (shared as a written spec with the CUDA side, not as code):
   D = odd; the block index m drops the top qubit.
 
 Parity status: every function here is pinned by tests in
-``tests/test_oracle.py`` (closed forms, algebraic identities, brute force and
+``tests/test_oracle.py`` and ``tests/test_oracle_spin.py`` (closed forms, algebraic identities, brute force and
 library special cases); none is "parity unpinned".
 """

@@ -16,6 +16,15 @@ Workload recipe (the paper's ensemble, main text around Eq. (1)):
   * a typical (Haar-like) state is an i.i.d. complex Gaussian vector over the
     full 2^(N/2) space, normalised over the full space; its two parity blocks
     are returned separately and are *not* renormalised.
+
+Spin-chain inputs (the outlook's sparse spin chains): Pauli strings given as
+two L-bit masks (x, z) -- on qubit q, x only = sigma_x, z only = sigma_z,
+both = sigma_y -- with real weights h.  The many-body-localisation workload
+is the random-field Heisenberg chain
+  H = J sum_i S_i . S_{i+1} - sum_i h_i S^z_i,  S = sigma / 2,
+  h_i uniform in [-W, W] (PCG64(2000 + r)), periodic unless stated,
+written as the strings X_i X_{i+1}, Y_i Y_{i+1}, Z_i Z_{i+1} (weight J/4) and
+Z_i (weight -h_i/2).
 """
 from __future__ import annotations
 
@@ -31,6 +40,9 @@ __all__ = [
     "random_state",
     "philox4x32_10",
     "philox_state",
+    "pauli_mask",
+    "heisenberg_chain",
+    "random_pauli_terms",
 ]
 
 
@@ -136,3 +148,56 @@ def philox_state(N: int, seed: int, state_id: int, idx=None):
     u2 = b.astype(np.float64) * 2.0 ** -53
     r = np.sqrt(-2.0 * np.log(u1))
     return r * np.cos(2 * np.pi * u2) + 1j * r * np.sin(2 * np.pi * u2)
+
+
+# ------------------------------------------------------------ spin chains --
+def pauli_mask(ops: dict):
+    """{qubit: 'X'|'Y'|'Z'} -> (x, z) masks of the string (identity elsewhere)."""
+    x = z = 0
+    for q, op in ops.items():
+        if op in ("X", "Y"):
+            x |= 1 << q
+        if op in ("Z", "Y"):
+            z |= 1 << q
+    return x, z
+
+
+def heisenberg_chain(L: int, W: float, r: int = 0, J: float = 1.0, periodic: bool = True, seed: int | None = None):
+    """Random-field Heisenberg chain on L qubits as Pauli strings.
+
+    Returns (x uint32 [T], z uint32 [T], h float64 [T], fields [L]).
+    """
+    rng = np.random.Generator(np.random.PCG64(2000 + r if seed is None else seed))
+    fields = rng.uniform(-W, W, size=L)
+    xs, zs, hs = [], [], []
+    bonds = [(i, i + 1) for i in range(L - 1)]
+    if periodic and L > 2:
+        bonds.append((L - 1, 0))
+    for i, j in bonds:
+        for op in "XYZ":
+            x, z = pauli_mask({i: op, j: op})
+            xs.append(x)
+            zs.append(z)
+            hs.append(J / 4.0)
+    for i in range(L):
+        x, z = pauli_mask({i: "Z"})
+        xs.append(x)
+        zs.append(z)
+        hs.append(-fields[i] / 2.0)
+    return (np.array(xs, dtype=np.uint32), np.array(zs, dtype=np.uint32), np.array(hs, dtype=np.float64),
+            fields)
+
+
+def random_pauli_terms(L: int, T: int, seed: int, max_weight: int = 4):
+    """T random Pauli strings of 1..max_weight non-identity letters (uniform
+    letters, distinct qubits) with N(0, 1) weights; duplicates are possible.
+    Returns (x uint32 [T], z uint32 [T], h float64 [T])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xs, zs = [], []
+    for _ in range(T):
+        w = int(rng.integers(1, min(max_weight, L) + 1))
+        qs = rng.choice(L, size=w, replace=False)
+        x, z = pauli_mask({int(q): "XYZ"[int(rng.integers(0, 3))] for q in qs})
+        xs.append(x)
+        zs.append(z)
+    return np.array(xs, dtype=np.uint32), np.array(zs, dtype=np.uint32), rng.normal(size=T)
