@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="all", choices=["all", "otoc-batch", "otoc-serve", "n64-otoc"],
-                    help="all: the benchmark line; otoc-batch / otoc-serve: only that leg, as its own JSON line")
+    ap.add_argument("--mode", default="all", choices=["all", "otoc-batch", "otoc-serve", "n64-otoc", "spin"],
+                    help="all: the benchmark line; otoc-batch / otoc-serve / n64-otoc / spin: only that leg, as "
+                         "its own JSON line (spin: random-field Heisenberg chain, H psi and OTOC curves)")
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--k", type=float, default=4.0)
     ap.add_argument("--no-fp64", action="store_true")
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-tmax", type=float, default=20.0)
     ap.add_argument("--serve-dt", type=float, default=1.0)
+    ap.add_argument("--spin-L", type=int, default=31, help="spin leg: qubits of the H psi chain (D = 2^L)")
+    ap.add_argument("--spin-otoc-L", type=int, default=20, help="spin leg: qubits of the OTOC-curve chain")
     ap.add_argument("--serve-load", type=float, default=0.75,
                     help="Poisson arrival rate as a fraction of the closed-loop capacity (all requests at t=0)")
     return ap.parse_args()
@@ -289,6 +292,104 @@ def otoc_served(args, syk, torch):
                  "workload": f"{n} Poisson requests, N 28..48 (P ~ 0.7^((N-28)/2)), k 0.5..4, beta 2..20, "
                              f"t 0..{args.serve_tmax:g} step {args.serve_dt:g}, c64, HBM budget 100 GB"})
     return summ
+
+
+# ------------------------------------------------------------- spin chains --
+def oracle_spin_rows_rate(L, W, seconds=10.0, seed=77):
+    """CPU oracle: sampled rows of H psi for the random-field Heisenberg chain
+    from the definition (basis-state maps, numpy).  Returns (Gterm*amp/s,
+    rows, T)."""
+    import numpy as np
+
+    import syk_inputs as si
+    from oracle import spin
+
+    x, z, h, _ = si.heisenberg_chain(L, W, r=0)
+    rng = np.random.default_rng(seed)
+
+    def run(nrows):
+        rows = rng.integers(0, 1 << L, nrows).astype(np.uint64)
+        needed = []
+        spin.rows_of_Hpsi(L, x, z, h, rows, lambda g: needed.append(g.copy()) or np.zeros(len(g)))
+        idx = np.unique(np.concatenate(needed))
+        vals = si.philox_state(2 * L + 2, seed, 0, idx)  # inputs, generated outside the timed region
+        t0 = time.perf_counter()
+        spin.rows_of_Hpsi(L, x, z, h, rows, lambda g: vals[np.searchsorted(idx, g)])
+        return time.perf_counter() - t0
+
+    dt = run(256)
+    nrows = int(min(1 << 20, max(256, 256 * seconds / max(dt, 1e-3))))
+    dt = run(nrows)
+    return len(h) * nrows / dt / 1e9, nrows, len(h)
+
+
+def spin_leg(args, syk, si, torch):
+    """The outlook's spin chains: the random-field Heisenberg chain
+    H = sum S_i.S_{i+1} - sum h_i S^z_i (periodic, W = 5) as Pauli strings.
+    H psi at L = spin_L (complex64 and complex128, inputs resident), and
+    OTOC curves (W = Z_0, V = Z_{L/2}, beta = 10, t = 0..10 in 10 segments,
+    one Philox state) at L = spin_otoc_L."""
+    import numpy as np
+
+    Wd = 5.0
+    L = args.spin_L
+    x, z, h, _ = si.heisenberg_chain(L, Wd, r=0)
+    out = {"workload": f"random-field Heisenberg chain, L={L}, W={Wd:g}, periodic, D=2^{L}"}
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    for dtype, steps in (("c64", args.steps), ("c128", max(1, min(3, args.steps)))):
+        with syk.PauliTerms(L, x, z, h, dtype=dtype) as t:
+            psi, _ = t.random_state(seed=1234, state_id=0, blocks=(0,))
+            o = t.empty()
+            if dtype == "c64":
+                clocks.start()
+            dt = time_matvecs(t, psi, o, steps, args.warmup if dtype == "c64" else 1, torch)
+            if dtype == "c64":
+                out["clocks"] = clocks.stop()
+            out[dtype] = {"Gtermamp_s": t.n_terms * t.D * steps / dt / 1e9, "ms_per_Hpsi": dt * 1e3 / steps,
+                          "terms": t.n_terms, "passes": t.info["n_passes"], "tile_reads": t.info["n_tile_reads"],
+                          "steps": steps}
+            del psi, o
+        torch.cuda.empty_cache()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    peak_slots = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
+    ms = out["c64"]["ms_per_Hpsi"]
+    T, D = out["c64"]["terms"], 1 << L
+    out["roofline_c64"] = {"bound": "alu", "achieved": ISSUE_SLOTS_PER_TERM_AMP * T * D / (ms / 1e3) / 1e12,
+                           "peak": peak_slots, "unit": "Tslot/s",
+                           "frac": ISSUE_SLOTS_PER_TERM_AMP * T * D / (ms / 1e3) / 1e12 / peak_slots,
+                           "hbm_gbs_achieved": 2 * D * 8 / (ms / 1e3) / 1e9,
+                           "hbm_peak_gbs": peaks.get("hbm_gbs", 6400.0), "algorithmic_bytes": 2 * D * 8}
+    # OTOC curves
+    Lo = args.spin_otoc_L
+    xo, zo, ho, _ = si.heisenberg_chain(Lo, Wd, r=1)
+    Wm, Vm = si.pauli_mask({0: "Z"}), si.pauli_mask({Lo // 2: "Z"})
+    grid = np.linspace(0.0, 10.0, 11)
+    curves = {}
+    for dtype in ("c64", "c128"):
+        with syk.PauliTerms(Lo, xo, zo, ho, dtype=dtype) as t:
+            t.pauli_otoc(Wm, Vm, 10.0, grid[:2], n_states=1, seed=5)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            F, o, st = t.pauli_otoc(Wm, Vm, 10.0, grid, n_states=1, seed=5)
+            wall = time.perf_counter() - t0
+            curves[dtype] = {"s_per_curve": wall, "matvecs": st.matvecs, "otoc": list(o), "F": F[0]}
+    diff = float(np.max(np.abs(curves["c64"]["F"] - curves["c128"]["F"])))
+    for c in curves.values():
+        c.pop("F")
+    out["otoc"] = {"workload": f"L={Lo}, W={Wd:g}, W=Z_0, V=Z_{Lo // 2}, beta=10, t=0..10 (11 points), "
+                               "one Philox state, Lanczos defaults (m=20 c64, m=30 c128)",
+                   **curves, "c64_vs_c128_max_abs_F_diff": diff}
+    if not args.no_cpu:
+        v, nrows, Tc = oracle_spin_rows_rate(L, Wd)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{nrows} random rows of H psi (L={L}, T={Tc}) from the definition"}
+    return out
 
 
 # ------------------------------------------------------------------ ours ----
@@ -542,6 +643,13 @@ def otoc_only(args):
                            "wall_s": wall, "matvecs": st.matvecs,
                            "substeps": st.substeps, "F": [[z.real, z.imag] for z in F[0]], "otoc": list(o),
                            "s_per_matvec": wall / max(1, st.matvecs)}}
+        print(json.dumps(line), flush=True)
+        return
+    if args.mode == "spin":
+        res = spin_leg(args, syk, si, torch)
+        line = {"metric": "spin-chain H·ψ Gterm·amp/s (random-field Heisenberg, complex64)",
+                "value": res["c64"]["Gtermamp_s"], "unit": UNIT, "higher_is_better": True, "steps": args.steps,
+                "warmup": args.warmup, "dtype": "c64 (f32 states)", "data": "synthetic", "config": res}
         print(json.dumps(line), flush=True)
         return
     if args.mode == "otoc-batch":

@@ -60,7 +60,7 @@ enum {
   SYK_EAGAIN = -6    /* no free slot or memory right now (batched engine); retry later */
 };
 enum { SYK_C64 = 0, SYK_C128 = 1 };
-enum { SYK_REP_JW = 0, SYK_REP_PAPER = 1 };
+enum { SYK_REP_JW = 0, SYK_REP_PAPER = 1, SYK_REP_PAULI = 2 /* Pauli-string handle (syk_build_pauli_terms) */ };
 enum { SYK_BLOCK_U = 0, SYK_BLOCK_D = 1 };
 enum { SYK_OTOC_TYPICAL = 0, SYK_OTOC_EXACT_TRACE = 1 };
 
@@ -296,6 +296,84 @@ int syk_krylov_evolve_noalloc(const syk_terms_t* h, int block, double tau, doubl
 int syk_otoc(const syk_terms_t* h, int a, int b, double beta, const double* t_grid, int n_t, int mode,
              int n_states, uint64_t seed, const void* psi_opt, const syk_krylov_params* p, double* F_raw,
              double* otoc, syk_krylov_stats* stats, syk_stream_t stream);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Pauli-string (spin-chain) Hamiltonians.  The paper's conclusions name OTOCs
+ * of sparse spin chains, such as those of many-body-localisation studies, as
+ * the next use of its GPU machinery; the supplement (Sec. I.A) stores every
+ * operator as a list of Pauli strings with coefficients.  These calls take
+ * such a list directly, H = sum_t h_t P_t on n_qubits qubits, and run it
+ * through the same H psi, Krylov and OTOC kernels as the SYK handles.
+ *   * A string is two masks: on qubit q (bit q of a basis index), x_q alone
+ *     = sigma_x, z_q alone = sigma_z, both = sigma_y = [[0,-i],[i,0]]; no bit
+ *     = identity.  h_t is real, so H is Hermitian.  With k = popc(x & z),
+ *     P = i^k X^x Z^z and (P psi)[m] = (-i)^k (-1)^{popc(z & m)} psi[m ^ x].
+ *   * The handle's state space is all 2^n_qubits amplitudes: D = 2^n_qubits,
+ *     L = n_qubits.  It holds no Majoranas (info.N = 0, info.rep =
+ *     SYK_REP_PAULI), so syk_apply_chi, syk_otoc and syk_batch_submit refuse
+ *     it; syk_apply_H, syk_krylov_evolve[_noalloc], syk_random_state (block
+ *     U) and syk_terms_* accept it with block SYK_BLOCK_U (both block slots
+ *     hold the same operator).
+ * ---------------------------------------------------------------------------
+ */
+
+/*
+ * syk_build_pauli_terms — compile H = sum_t h[t] P(x[t], z[t]).
+ *   n_qubits : 1 <= n_qubits <= 31.
+ *   x, z     : HOST uint32 [T], masks below 2^n_qubits.
+ *   h        : HOST double [T], finite.
+ *   dtype    : SYK_C64 or SYK_C128.
+ * Equal strings are merged and zero sums dropped; the table, pass plan and
+ * records are built and uploaded to the current device as for
+ * syk_build_terms (T = 0 gives H = 0).  Errors: SYK_EINVAL (n_qubits out of
+ * range, a mask with bits at or above n_qubits, non-finite h, null array),
+ * SYK_ENOMEM, SYK_ECUDA.
+ */
+int syk_build_pauli_terms(int n_qubits, int64_t T, const uint32_t* x, const uint32_t* z, const double* h,
+                          int dtype, syk_terms_t** out);
+
+/*
+ * Host-only compilation of syk_build_pauli_terms (no CUDA call).  Writes up
+ * to `capacity` compiled strings into the HOST arrays (any may be NULL) and
+ * the count into *n_terms: flip mask, sign mask, coefficient and imag flag
+ * in the form (H psi)[m] = sum_t coef[t] (imag ? i : 1) (-1)^{popc(z & m)}
+ * psi[m ^ x] — the form syk_terms_export reports for a Pauli handle.
+ */
+int syk_compile_pauli_host(int n_qubits, int64_t T, const uint32_t* x, const uint32_t* z, const double* h,
+                           int64_t capacity, int64_t* n_terms, uint32_t* x_out, uint32_t* z_out, double* coef,
+                           uint8_t* imag);
+
+/*
+ * syk_apply_pauli — out = P(x, z) psi (coefficient 1) for nstates states of
+ * a Pauli handle; psi, out: [nstates][D] device.  out may alias psi exactly
+ * when x = 0 (a diagonal string); otherwise they must not overlap.
+ * Errors: SYK_EINVAL (not a Pauli handle, mask out of range, null or
+ * misaligned pointer, overlap), SYK_ECUDA.
+ */
+int syk_apply_pauli(const syk_terms_t* h, uint32_t x, uint32_t z, const void* psi, void* out, int64_t nstates,
+                    syk_stream_t stream);
+
+/*
+ * syk_pauli_otoc — the regularised OTOC of Eq. (2) with the Majoranas
+ * replaced by two Pauli strings W = P(w_x, w_z) and V = P(v_x, v_z), on a
+ * single state (the supplement's symmetric beta/8 + beta/8 split):
+ *   F(t) = <psi| e^{(it-b/8)H} W e^{-(it+b/4)H} V e^{(it-b/4)H} W
+ *          e^{-(it+b/4)H} V e^{-bH/8} |psi>,
+ *   OTOC(t) = Re mean_s F_s(t) / Re mean_s F_s(0).
+ * mode SYK_OTOC_TYPICAL: states from psi_opt (DEVICE [n_states][D], used as
+ * given), else syk_random_state(seed, s) block U normalised over its D
+ * amplitudes; SYK_OTOC_EXACT_TRACE: all D basis states, F = Tr[...]/D (one
+ * row).  t_grid (HOST, non-decreasing), F_raw (HOST [rows][n_t][2]), otoc
+ * (HOST [n_t]), p, stats and the blocking behaviour are as for syk_otoc; the
+ * call allocates its own device workspace and frees it before returning.
+ * Errors: SYK_EINVAL (not a Pauli handle, mask out of range, bad grid, beta,
+ * mode or n_states), SYK_ENOMEM, SYK_ENOCONV, SYK_ECUDA.
+ */
+int syk_pauli_otoc(const syk_terms_t* h, uint32_t w_x, uint32_t w_z, uint32_t v_x, uint32_t v_z, double beta,
+                   const double* t_grid, int n_t, int mode, int n_states, uint64_t seed, const void* psi_opt,
+                   const syk_krylov_params* p, double* F_raw, double* otoc, syk_krylov_stats* stats,
+                   syk_stream_t stream);
 
 /*
  * Batched OTOC engine — many (realisation, state) OTOC curves at once.

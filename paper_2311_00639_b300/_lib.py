@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(HERE, "libsyk.so")
 
 SYK_OK, SYK_EINVAL, SYK_ENOMEM, SYK_ENOCONV, SYK_ETIMEOUT, SYK_ECUDA, SYK_EAGAIN = 0, -1, -2, -3, -4, -5, -6
 SYK_C64, SYK_C128 = 0, 1
-SYK_REP_JW, SYK_REP_PAPER = 0, 1
+SYK_REP_JW, SYK_REP_PAPER, SYK_REP_PAULI = 0, 1, 2
 SYK_OTOC_TYPICAL, SYK_OTOC_EXACT_TRACE = 0, 1
 
 
@@ -71,6 +71,11 @@ SIGNATURES = {
                                        C.POINTER(KrylovStats), _P]),
     "syk_otoc": (_I, [_P, _I, _I, _D, _P, _I, _I, _I, _U64, _P, C.POINTER(KrylovParams), _P, _P,
                       C.POINTER(KrylovStats), _P]),
+    "syk_build_pauli_terms": (_I, [_I, _I64, _P, _P, _P, _I, C.POINTER(_P)]),
+    "syk_compile_pauli_host": (_I, [_I, _I64, _P, _P, _P, _I64, C.POINTER(_I64), _P, _P, _P, _P]),
+    "syk_apply_pauli": (_I, [_P, C.c_uint32, C.c_uint32, _P, _P, _I64, _P]),
+    "syk_pauli_otoc": (_I, [_P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, _D, _P, _I, _I, _I, _U64, _P,
+                            C.POINTER(KrylovParams), _P, _P, C.POINTER(KrylovStats), _P]),
     "syk_batch_create": (_I, [_I, _I, _SZ, C.POINTER(KrylovParams), C.POINTER(_P)]),
     "syk_batch_destroy": (_I, [_P]),
     "syk_batch_submit": (_I, [_P, C.POINTER(OtocJob)]),

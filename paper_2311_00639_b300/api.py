@@ -92,6 +92,33 @@ def plan_host(N: int, quads, J, dtype: str = "c64", rep: str = "jw", l2_budget_b
     return out
 
 
+def _pauli_arrays(x, z, h):
+    xa = np.ascontiguousarray(np.asarray(x, dtype=np.uint32).reshape(-1))
+    za = np.ascontiguousarray(np.asarray(z, dtype=np.uint32).reshape(-1))
+    ha = np.ascontiguousarray(np.asarray(h, dtype=np.float64).reshape(-1))
+    if not (xa.shape == za.shape == ha.shape):
+        raise ValueError("x, z and h lengths differ")
+    return xa, za, ha
+
+
+def compile_pauli_host(n_qubits: int, x, z, h) -> dict:
+    """Host-only compilation of a Pauli-string Hamiltonian (no GPU): x, z,
+    coef, imag arrays with (H psi)[m] = sum coef (imag ? i : 1)
+    (-1)^{popc(z & m)} psi[m ^ x]."""
+    lib = L.load()
+    xa, za, ha = _pauli_arrays(x, z, h)
+    n = C.c_int64(0)
+    L.check(lib.syk_compile_pauli_host(n_qubits, len(ha), xa.ctypes.data, za.ctypes.data, ha.ctypes.data, 0,
+                                       C.byref(n), None, None, None, None))
+    cnt = n.value
+    out = {"x": np.zeros(cnt, np.uint32), "z": np.zeros(cnt, np.uint32), "coef": np.zeros(cnt),
+           "imag": np.zeros(cnt, np.uint8)}
+    L.check(lib.syk_compile_pauli_host(n_qubits, len(ha), xa.ctypes.data, za.ctypes.data, ha.ctypes.data, cnt,
+                                       C.byref(n), out["x"].ctypes.data, out["z"].ctypes.data,
+                                       out["coef"].ctypes.data, out["imag"].ctypes.data))
+    return out
+
+
 def compile_chi_host(N: int, n: int, rep: str = "jw") -> dict:
     lib = L.load()
     x, z = C.c_uint32(0), C.c_uint32(0)
@@ -316,6 +343,59 @@ class Terms:
         L.check(self._lib.syk_otoc(self._h, a, b, float(beta), tg.ctypes.data, len(tg), md, int(n_states),
                                    C.c_uint64(seed), None if psi is None else _ptr(psi), C.byref(p),
                                    F.ctypes.data, o.ctypes.data, C.byref(st), _stream(stream)))
+        return F[..., 0] + 1j * F[..., 1], o, KrylovStats(st)
+
+
+class PauliTerms(Terms):
+    """A Pauli-string (spin-chain) Hamiltonian H = sum_t h_t P(x_t, z_t) on
+    n_qubits qubits, resident on the current CUDA device
+    (syk_build_pauli_terms).  A string is two masks: on qubit q, x alone =
+    sigma_x, z alone = sigma_z, both = sigma_y.  States have D = 2^n_qubits
+    amplitudes; apply_H / krylov_evolve take block 0.  The Majorana calls
+    (apply_chi, otoc, Batch.submit) refuse this handle."""
+
+    def __init__(self, n_qubits: int, x, z, h, dtype: str = "c64"):
+        self._lib = L.load()
+        xa, za, ha = _pauli_arrays(x, z, h)
+        hd = C.c_void_p()
+        L.check(self._lib.syk_build_pauli_terms(int(n_qubits), len(ha), xa.ctypes.data, za.ctypes.data,
+                                                ha.ctypes.data, _DT[dtype], C.byref(hd)))
+        self._h = hd
+        self.N, self.dtype, self.rep, self.n_qubits = 0, dtype, "pauli", int(n_qubits)
+        info = L.TermsInfo()
+        L.check(self._lib.syk_terms_get_info(hd, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in L.TermsInfo._fields_}
+        self.D = info.D
+        self.n_terms = info.n_terms
+
+    def apply_pauli(self, x: int, z: int, psi, out=None, stream=None):
+        """out = P(x, z) psi (coefficient 1)."""
+        ns = self._check_vec(psi)
+        out = _torch().empty_like(psi) if out is None else out
+        self._check_vec(out)
+        L.check(self._lib.syk_apply_pauli(self._h, int(x), int(z), _ptr(psi), _ptr(out), ns, _stream(stream)))
+        return out
+
+    def pauli_otoc(self, W, V, beta: float, t_grid, mode: str = "typical", n_states: int = 1, seed: int = 0,
+                   psi=None, stream=None, **kp):
+        """Regularised OTOC of Eq. (2) with Pauli strings W = (x, z) and
+        V = (x, z).  Returns (F_raw complex [rows, n_t], otoc [n_t], KrylovStats).
+
+        psi: optional CUDA tensor [n_states, D] of states, used as given.
+        """
+        tg = np.ascontiguousarray(np.asarray(t_grid, dtype=np.float64))
+        md = L.SYK_OTOC_EXACT_TRACE if mode == "exact" else L.SYK_OTOC_TYPICAL
+        if psi is not None:
+            n_states = self._check_vec(psi)
+        rows = 1 if md == L.SYK_OTOC_EXACT_TRACE else n_states
+        F = np.zeros((rows, len(tg), 2))
+        o = np.zeros(len(tg))
+        p = _params(**kp)
+        st = L.KrylovStats()
+        L.check(self._lib.syk_pauli_otoc(self._h, int(W[0]), int(W[1]), int(V[0]), int(V[1]), float(beta),
+                                         tg.ctypes.data, len(tg), md, int(n_states), C.c_uint64(seed),
+                                         None if psi is None else _ptr(psi), C.byref(p), F.ctypes.data,
+                                         o.ctypes.data, C.byref(st), _stream(stream)))
         return F[..., 0] + 1j * F[..., 1], o, KrylovStats(st)
 
 
