@@ -367,6 +367,11 @@ int syk_apply_pauli(const syk_terms_t* h, uint32_t x, uint32_t z, const void* ps
  * row).  t_grid (HOST, non-decreasing), F_raw (HOST [rows][n_t][2]), otoc
  * (HOST [n_t]), p, stats and the blocking behaviour are as for syk_otoc; the
  * call allocates its own device workspace and frees it before returning.
+ * F is not normalised: its size grows like e^{beta |E_min|}, and a spin
+ * chain's energies are extensive, so complex64 states overflow once
+ * beta |E_min| exceeds about 80.  Adding the identity string (x = z = 0) with
+ * weight c to H multiplies every F(t) by e^{-beta c} exactly and leaves the
+ * OTOC ratio unchanged; c near -E_min keeps the weights in range.
  * Errors: SYK_EINVAL (not a Pauli handle, mask out of range, bad grid, beta,
  * mode or n_states), SYK_ENOMEM, SYK_ENOCONV, SYK_ECUDA.
  */

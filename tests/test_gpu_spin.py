@@ -214,7 +214,11 @@ def test_pauli_otoc_exact_trace_and_closed_form():
         assert np.allclose(F[0], np.cos(4 * hh * tg), atol=1e-12)
 
 
-def test_pauli_otoc_complex64_against_oracle():
+def test_pauli_otoc_complex64_against_oracle_and_shift():
+    """complex64 states against the oracle (relative to the largest |F|: the
+    raw F of a spin chain grows like e^{beta |E_min|}), and the identity-string
+    shift H -> H + c that keeps complex64 weights in range: F -> e^{-beta c} F
+    exactly, the OTOC ratio unchanged."""
     import paper_2311_00639_b300 as syk
 
     L = 12
@@ -224,11 +228,19 @@ def test_pauli_otoc_complex64_against_oracle():
     V = si.pauli_mask({6: "Z"})
     X = {0: spin.pauli_dense(L, *W), 1: spin.pauli_dense(L, *V)}
     ts = [0.0, 1.0, 2.5]
+    beta, c = 4.0, 9.0
     psi = _state(1 << L, 10)
-    ref = ot.F_state(Hd, X, 0, 1, 4.0, ts, psi)
+    ref = ot.F_state(Hd, X, 0, 1, beta, ts, psi)
     with syk.PauliTerms(L, x, z, h, dtype="c64") as t:
-        F, _, _ = t.pauli_otoc(W, V, 4.0, ts, psi=_dev(psi[None, :], "c64"))
-        assert np.max(np.abs(F[0] - ref)) < 1e-4
+        F, o, _ = t.pauli_otoc(W, V, beta, ts, psi=_dev(psi[None, :], "c64"))
+        assert _rel(F[0], ref) < 1e-4
+        assert np.allclose(o, ref.real / ref.real[0], atol=1e-4)
+    xs, zs, hs = np.append(x, 0), np.append(z, 0), np.append(h, c)
+    for dtype, lim in (("c64", 1e-4), ("c128", 1e-10)):
+        with syk.PauliTerms(L, xs, zs, hs, dtype=dtype) as t:
+            F, o, _ = t.pauli_otoc(W, V, beta, ts, psi=_dev(psi[None, :], dtype))
+            assert _rel(F[0], np.exp(-beta * c) * ref) < lim, dtype
+            assert np.allclose(o, ref.real / ref.real[0], atol=lim)
 
 
 def test_majorana_calls_refuse_a_pauli_handle():
@@ -247,7 +259,14 @@ def test_majorana_calls_refuse_a_pauli_handle():
                 b.submit(t, 1, 0, 1.0, [0.0], 0, 0, 0)
         with pytest.raises(L.SykError):
             t.apply_pauli(1 << 6, 0, psi)  # qubit 6 of a 6-qubit chain
+    import ctypes as C
+
+    import torch
+
     q, J, _ = si.sample_sparse_syk(12, 4)
-    with syk.Terms(12, q, J, dtype="c128") as ts:
-        with pytest.raises(L.SykError):
-            ts.apply_pauli(1, 0, _dev(_state(32, 2), "c128"))
+    with syk.Terms(12, q, J, dtype="c128") as ts:  # syk_apply_pauli takes Pauli handles only
+        v = _dev(_state(32, 2), "c128")
+        o = torch.empty_like(v)
+        rc = L.load().syk_apply_pauli(ts._h, 1, 0, C.c_void_p(v.data_ptr()), C.c_void_p(o.data_ptr()), 1,
+                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == L.SYK_EINVAL
