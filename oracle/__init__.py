@@ -23,7 +23,11 @@ paper (arXiv 2311.00639) for obviousness, not speed:
 * ``spin``        Pauli-string (spin-chain) Hamiltonians of the paper's
                   outlook: dense Kronecker products, basis-state maps, CSR
                   and sampled rows; their OTOC is ``otoc`` with W, V given
-                  as matrices.
+                  as matrices;
+* ``nonherm``     non-Hermitian sparse SYK (complex couplings), the other
+                  model of the outlook: dense / CSR matrices, scipy expm
+                  evolution, and the infinite-temperature OTOC with
+                  W(t) = e^{iH^dag t} W e^{-iHt}.
 
 Conventions (shared as a written spec with the CUDA side, not as code):
   qubit s <-> bit s of the basis index; operators are Kronecker products
@@ -37,6 +41,7 @@ Conventions (shared as a written spec with the CUDA side, not as code):
   D = odd; the block index m drops the top qubit.
 
 Parity status: every function here is pinned by tests in
-``tests/test_oracle.py`` and ``tests/test_oracle_spin.py`` (closed forms, algebraic identities, brute force and
+``tests/test_oracle.py``, ``tests/test_oracle_spin.py`` and
+``tests/test_oracle_nonherm.py`` (closed forms, algebraic identities, brute force and
 library special cases); none is "parity unpinned".
 """
