@@ -43,9 +43,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="all", choices=["all", "otoc-batch", "otoc-serve", "n64-otoc", "spin"],
-                    help="all: the benchmark line; otoc-batch / otoc-serve / n64-otoc / spin: only that leg, as "
-                         "its own JSON line (spin: random-field Heisenberg chain, H psi and OTOC curves)")
+    ap.add_argument("--mode", default="all",
+                    choices=["all", "otoc-batch", "otoc-serve", "n64-otoc", "spin", "nonherm"],
+                    help="all: the benchmark line; otoc-batch / otoc-serve / n64-otoc / spin / nonherm: only that "
+                         "leg, as its own JSON line (spin: random-field Heisenberg chain, H psi and OTOC curves; "
+                         "nonherm: non-Hermitian SYK, H psi and Arnoldi OTOC curves)")
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--k", type=float, default=4.0)
     ap.add_argument("--no-fp64", action="store_true")
@@ -404,6 +406,50 @@ def spin_leg(args, syk, si, torch):
     return out
 
 
+# --------------------------------------------------------- non-Hermitian ----
+def nonherm_leg(args, syk, si, torch):
+    """Non-Hermitian sparse SYK (couplings J + iM, M drawn like J): H psi at
+    N = args.N (complex64, inputs resident; every term is a real-class and an
+    imaginary-class string) and infinite-temperature OTOC curves
+    (W(t) = e^{iH^dag t} W e^{-iHt}, a = N-1, b = N-2, t = 0..10 in 10
+    segments, one Philox state, Arnoldi) at N = 30, k = 3."""
+    import numpy as np
+
+    def couplings(N, k, r):
+        q, J, _ = si.sample_sparse_syk(N, k, r=r)
+        M = np.random.default_rng(900 + r).normal(size=len(J)) * math.sqrt(float(np.mean(J ** 2)))
+        return q, J, M
+
+    q, J, M = couplings(args.N, args.k, 0)
+    out = {"workload": f"non-Hermitian sparse SYK N={args.N}, k={args.k:g}, couplings J + iM, one parity block"}
+    with syk.Terms.complex(args.N, q, J, M, dtype="c64") as h:
+        psi, _ = h.random_state(seed=1234, state_id=0, blocks=(0,))
+        o = h.empty()
+        dt = time_matvecs(h, psi, o, args.steps, args.warmup, torch)
+        out["Hpsi_c64"] = {"Gtermamp_s": len(J) * h.D * args.steps / dt / 1e9, "ms_per_Hpsi": dt * 1e3 / args.steps,
+                           "quads": len(J), "strings": h.n_terms, "passes": h.info["n_passes"],
+                           "note": "rate counts input terms (quads); each compiles to two strings"}
+        del psi, o
+    torch.cuda.empty_cache()
+    grid = np.linspace(0.0, 10.0, 11)
+    q, J, M = couplings(30, 3.0, 1)
+    curves = {}
+    for dtype in ("c64", "c128"):
+        with syk.Terms.complex(30, q, J, M, dtype=dtype) as h:
+            h.otoc_nonhermitian(29, 28, grid[:2], n_states=1, seed=5)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            F, o, st = h.otoc_nonhermitian(29, 28, grid, n_states=1, seed=5)
+            curves[dtype] = {"s_per_curve": time.perf_counter() - t0, "matvecs": st.matvecs,
+                             "substeps": st.substeps, "otoc": list(o), "F": F[0]}
+    diff = float(np.max(np.abs(curves["c64"]["F"] - curves["c128"]["F"])) / np.max(np.abs(curves["c128"]["F"])))
+    for c in curves.values():
+        c.pop("F")
+    out["otoc"] = {"workload": "N=30, k=3, couplings J + iM, a=29, b=28, beta=0, t=0..10 (11 points), one Philox "
+                               "state, Arnoldi (m=20 c64, m=30 c128)", **curves, "c64_vs_c128_max_rel_F_diff": diff}
+    return out
+
+
 # ------------------------------------------------------------------ ours ----
 def build_lib():
     spec = importlib.util.spec_from_file_location("_syk_build", os.path.join(ROOT, "paper_2311_00639_b300", "build.py"))
@@ -662,6 +708,14 @@ def otoc_only(args):
         line = {"metric": "spin-chain H·ψ Gterm·amp/s (random-field Heisenberg, complex64)",
                 "value": res["c64"]["Gtermamp_s"], "unit": UNIT, "higher_is_better": True, "steps": args.steps,
                 "warmup": args.warmup, "dtype": "c64 (f32 states)", "data": "synthetic", "config": res}
+        print(json.dumps(line), flush=True)
+        return
+    if args.mode == "nonherm":
+        res = nonherm_leg(args, syk, si, torch)
+        line = {"metric": "non-Hermitian SYK H·ψ Gterm·amp/s (complex64) and Arnoldi OTOC curves",
+                "value": res["Hpsi_c64"]["Gtermamp_s"], "unit": UNIT, "higher_is_better": True,
+                "steps": args.steps, "warmup": args.warmup, "dtype": "c64 (f32 states)", "data": "synthetic",
+                "config": res}
         print(json.dumps(line), flush=True)
         return
     if args.mode == "otoc-batch":

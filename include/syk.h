@@ -381,6 +381,63 @@ int syk_pauli_otoc(const syk_terms_t* h, uint32_t w_x, uint32_t w_z, uint32_t v_
                    syk_stream_t stream);
 
 /*
+ * ---------------------------------------------------------------------------
+ * Non-Hermitian sparse SYK, the other model of the paper's outlook:
+ * H = sum_t (J_t + i M_t) chi_i chi_j chi_k chi_l (complex couplings, Eq. (1)
+ * otherwise unchanged), so H^dag = sum_t (J_t - i M_t) chi chi chi chi.  The
+ * handle runs on the same H psi kernels (each term splits into a real-class
+ * and an imaginary-class string); syk_krylov_evolve[_noalloc] on a handle
+ * with any M_t != 0 uses Arnoldi (full orthogonalisation, classical
+ * Gram-Schmidt twice, FP64 Hessenberg matrix, its exponential by scaling
+ * and squaring with a [6/6] Pade approximant on the device) with the same
+ * substep control as Lanczos; reorth and two_pass are refused for it, and
+ * its workspace is larger (syk_krylov_workspace_bytes).  syk_otoc and the
+ * batched engine refuse such a handle; use syk_otoc_nonhermitian.
+ * ---------------------------------------------------------------------------
+ */
+
+/*
+ * syk_build_terms_complex — as syk_build_terms with couplings J_re + i J_im
+ * (HOST double [T] each).  With J_im all zero the handle equals
+ * syk_build_terms(J_re) (Hermitian, Lanczos).  Errors as syk_build_terms.
+ */
+int syk_build_terms_complex(int N, int64_t T, const int32_t* quads, const double* J_re, const double* J_im, int dtype,
+                            int rep, syk_terms_t** out);
+
+/* Host-only compilation of syk_build_terms_complex, in the form of
+ * syk_compile_terms_host (no CUDA call). */
+int syk_compile_terms_complex_host(int N, int64_t T, const int32_t* quads, const double* J_re, const double* J_im,
+                                   int rep, int64_t capacity, int64_t* n_terms, uint32_t* x, uint32_t* z,
+                                   double* coef_U, double* coef_D, uint8_t* imag);
+
+/* *hermitian = 1 if the handle's Krylov propagation is Lanczos, 0 if Arnoldi. */
+int syk_terms_is_hermitian(const syk_terms_t* h, int* hermitian);
+
+/*
+ * syk_terms_adjoint — a new handle for H^dag on the current device (same N,
+ * representation, dtype; Pauli handles too).  A block string
+ * c (imag ? i : 1) S with S[m, m ^ x] = (-1)^{popc(z & m)} has adjoint
+ * conj(c (imag ? i : 1)) (-1)^{popc(x & z)} S.  The caller destroys it.
+ */
+int syk_terms_adjoint(const syk_terms_t* h, syk_terms_t** out);
+
+/*
+ * syk_otoc_nonhermitian — the OTOC of Eq. (2) at infinite temperature with
+ * the Heisenberg-picture operator W(t) = e^{iH^dag t} W e^{-iHt} (the paper
+ * gives no formula for non-Hermitian H; with M = 0 this is syk_otoc at
+ * beta = 0):
+ *   F_P(t) = <psi_P| e^{iH^dag t} chi_a e^{-iH_QQ t} chi_b e^{iH^dag_PP t}
+ *            chi_a e^{-iH_QQ t} chi_b |psi_P>,  F = F_U + F_D,
+ *   OTOC(t) = Re mean_s F_s(t) / Re mean_s F_s(0).
+ * Arguments, modes, outputs and blocking as for syk_otoc without beta;
+ * H^dag is built internally (syk_terms_adjoint) for the call.  Errors:
+ * SYK_EINVAL, SYK_ENOMEM, SYK_ENOCONV, SYK_ECUDA.
+ */
+int syk_otoc_nonhermitian(const syk_terms_t* h, int a, int b, const double* t_grid, int n_t, int mode, int n_states,
+                          uint64_t seed, const void* psi_opt, const syk_krylov_params* p, double* F_raw, double* otoc,
+                          syk_krylov_stats* stats, syk_stream_t stream);
+
+/*
  * Batched OTOC engine — many (realisation, state) OTOC curves at once.
  * Each job is the typical-state OTOC of syk_otoc for one Hamiltonian handle
  * (any N, same dtype as the batch), one Philox state (syk_random_state(seed,

@@ -76,6 +76,12 @@ SIGNATURES = {
     "syk_apply_pauli": (_I, [_P, C.c_uint32, C.c_uint32, _P, _P, _I64, _P]),
     "syk_pauli_otoc": (_I, [_P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, _D, _P, _I, _I, _I, _U64, _P,
                             C.POINTER(KrylovParams), _P, _P, C.POINTER(KrylovStats), _P]),
+    "syk_build_terms_complex": (_I, [_I, _I64, _P, _P, _P, _I, _I, C.POINTER(_P)]),
+    "syk_compile_terms_complex_host": (_I, [_I, _I64, _P, _P, _P, _I, _I64, C.POINTER(_I64), _P, _P, _P, _P, _P]),
+    "syk_terms_is_hermitian": (_I, [_P, C.POINTER(_I)]),
+    "syk_terms_adjoint": (_I, [_P, C.POINTER(_P)]),
+    "syk_otoc_nonhermitian": (_I, [_P, _I, _I, _P, _I, _I, _I, _U64, _P, C.POINTER(KrylovParams), _P, _P,
+                                   C.POINTER(KrylovStats), _P]),
     "syk_batch_create": (_I, [_I, _I, _SZ, C.POINTER(KrylovParams), C.POINTER(_P)]),
     "syk_batch_destroy": (_I, [_P]),
     "syk_batch_submit": (_I, [_P, C.POINTER(OtocJob)]),

@@ -119,6 +119,25 @@ def compile_pauli_host(n_qubits: int, x, z, h) -> dict:
     return out
 
 
+def compile_terms_complex_host(N: int, quads, J_re, J_im, rep: str = "jw") -> dict:
+    """Host-only compilation with complex couplings J_re + i J_im (no GPU)."""
+    lib = L.load()
+    q, jr = _host_arrays(quads, J_re)
+    ji = np.ascontiguousarray(np.asarray(J_im, dtype=np.float64).reshape(-1))
+    if ji.shape != jr.shape:
+        raise ValueError("J_re and J_im lengths differ")
+    n = C.c_int64(0)
+    args = (N, q.shape[0], q.ctypes.data, jr.ctypes.data, ji.ctypes.data, _REP[rep])
+    L.check(lib.syk_compile_terms_complex_host(*args, 0, C.byref(n), None, None, None, None, None))
+    cnt = n.value
+    out = {"x": np.zeros(cnt, np.uint32), "z": np.zeros(cnt, np.uint32), "coef_U": np.zeros(cnt),
+           "coef_D": np.zeros(cnt), "imag": np.zeros(cnt, np.uint8)}
+    L.check(lib.syk_compile_terms_complex_host(*args, cnt, C.byref(n), out["x"].ctypes.data, out["z"].ctypes.data,
+                                               out["coef_U"].ctypes.data, out["coef_D"].ctypes.data,
+                                               out["imag"].ctypes.data))
+    return out
+
+
 def compile_chi_host(N: int, n: int, rep: str = "jw") -> dict:
     lib = L.load()
     x, z = C.c_uint32(0), C.c_uint32(0)
@@ -157,6 +176,71 @@ class Terms:
         self.info = {k: getattr(info, k) for k, _ in L.TermsInfo._fields_}
         self.D = info.D
         self.n_terms = info.n_terms
+
+    @classmethod
+    def _from_handle(cls, h, N: int, dtype: str, rep: str):
+        self = cls.__new__(cls)
+        self._lib = L.load()
+        self._h = h
+        self.N, self.dtype, self.rep = N, dtype, rep
+        info = L.TermsInfo()
+        L.check(self._lib.syk_terms_get_info(h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in L.TermsInfo._fields_}
+        self.D = info.D
+        self.n_terms = info.n_terms
+        return self
+
+    @classmethod
+    def complex(cls, N: int, quads, J_re, J_im, dtype: str = "c64", rep: str = "jw") -> "Terms":
+        """Non-Hermitian sparse SYK: couplings J_re + i J_im (syk_build_terms_complex).
+        krylov_evolve uses Arnoldi when any J_im is non-zero; the OTOC is
+        otoc_nonhermitian."""
+        lib = L.load()
+        q, jr = _host_arrays(quads, J_re)
+        ji = np.ascontiguousarray(np.asarray(J_im, dtype=np.float64).reshape(-1))
+        if ji.shape != jr.shape:
+            raise ValueError("J_re and J_im lengths differ")
+        h = C.c_void_p()
+        L.check(lib.syk_build_terms_complex(N, q.shape[0], q.ctypes.data, jr.ctypes.data, ji.ctypes.data, _DT[dtype],
+                                            _REP[rep], C.byref(h)))
+        return cls._from_handle(h, N, dtype, rep)
+
+    @property
+    def hermitian(self) -> bool:
+        v = C.c_int(0)
+        L.check(self._lib.syk_terms_is_hermitian(self._h, C.byref(v)))
+        return bool(v.value)
+
+    def adjoint(self) -> "Terms":
+        """A new handle for H^dagger (syk_terms_adjoint)."""
+        h = C.c_void_p()
+        L.check(self._lib.syk_terms_adjoint(self._h, C.byref(h)))
+        out = type(self)._from_handle(h, self.N, self.dtype, self.rep)
+        if hasattr(self, "n_qubits"):
+            out.n_qubits = self.n_qubits
+        return out
+
+    def otoc_nonhermitian(self, a: int, b: int, t_grid, mode: str = "typical", n_states: int = 1, seed: int = 0,
+                          psi=None, stream=None, **kp):
+        """Infinite-temperature OTOC with W(t) = e^{iH^dag t} W e^{-iHt}
+        (syk_otoc_nonhermitian).  Returns (F_raw complex [rows, n_t], otoc [n_t], KrylovStats).
+
+        psi: optional CUDA tensor [n_states, 2, D] (U then D block per state).
+        """
+        tg = np.ascontiguousarray(np.asarray(t_grid, dtype=np.float64))
+        md = L.SYK_OTOC_EXACT_TRACE if mode == "exact" else L.SYK_OTOC_TYPICAL
+        if psi is not None:
+            self._check_vec(psi)
+            n_states = psi.numel() // (2 * self.D)
+        rows = 1 if md == L.SYK_OTOC_EXACT_TRACE else n_states
+        F = np.zeros((rows, len(tg), 2))
+        o = np.zeros(len(tg))
+        p = _params(**kp)
+        st = L.KrylovStats()
+        L.check(self._lib.syk_otoc_nonhermitian(self._h, a, b, tg.ctypes.data, len(tg), md, int(n_states),
+                                                C.c_uint64(seed), None if psi is None else _ptr(psi), C.byref(p),
+                                                F.ctypes.data, o.ctypes.data, C.byref(st), _stream(stream)))
+        return F[..., 0] + 1j * F[..., 1], o, KrylovStats(st)
 
     # -- lifetime
     def close(self):

@@ -926,6 +926,7 @@ int syk_batch_submit(syk_batch_t* h, const syk_otoc_job* job) {
     const syk_terms* t = job->h;
     SYK_REQUIRE(t->dtype == b.dtype, "job Hamiltonian dtype differs from the batch dtype");
     SYK_REQUIRE(t->device == b.device, "job Hamiltonian lives on another device");
+    SYK_REQUIRE(t->hermitian, "the batched engine runs Hermitian Hamiltonians only (Lanczos)");
     SYK_REQUIRE(job->a >= 0 && job->a < t->N && job->b >= 0 && job->b < t->N, "Majorana index out of range");
     SYK_REQUIRE(job->n_t >= 1 && std::isfinite(job->beta) && job->beta >= 0, "bad n_t or beta");
     for (int n = 0; n < job->n_t; ++n) {

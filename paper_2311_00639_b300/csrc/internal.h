@@ -52,6 +52,10 @@ struct ChiString {
 void compile_terms(int N, int rep, int64_t T, const int32_t* quads, const double* J,
                    std::vector<BlockString>& out, int64_t& n_real, int64_t& n_xgroups);
 ChiString compile_chi(int N, int rep, int n);
+// Complex couplings J_re + i J_im (non-Hermitian SYK): each term's value
+// splits into a real-class and an imaginary-class string with the same masks.
+void compile_terms_complex(int N, int rep, int64_t T, const int32_t* quads, const double* J_re, const double* J_im,
+                           std::vector<BlockString>& out, int64_t& n_real, int64_t& n_xgroups);
 
 // Record the message syk_last_error() returns on this thread (capi.cu).
 void set_last_error(const std::string& msg);
@@ -150,6 +154,7 @@ struct syk_terms {
   size_t split_ws_bytes = 0;
   syk::PassPlan* d_pass_tail = nullptr;  // the last pass's tile order with no terms (epilogue after a split)
   int n_sm = 148;
+  bool hermitian = true;  // false: complex couplings; Krylov propagation uses Arnoldi
   syk_terms() = default;
   syk_terms(const syk_terms&) = delete;
   syk_terms& operator=(const syk_terms&) = delete;

@@ -84,6 +84,11 @@ struct KrylovResult {
   double err = 0.0;
 };
 size_t krylov_ws_bytes(const syk_terms* h, int m, bool two_pass);
+// Arnoldi engine for a non-Hermitian H (arnoldi.cu); krylov_* dispatch to it
+// when h->hermitian is false.
+size_t arnoldi_ws_bytes(const syk_terms* h, int m);
+KrylovResult arnoldi_evolve_one(const syk_terms* h, int block, double tau, double t, const void* x, void* y, int m,
+                                double tol, int max_substeps, void* ws, cudaStream_t st);
 // y = e^{-(tau + i t) H_P} x for one state; y may alias x.
 KrylovResult krylov_evolve_one(const syk_terms* h, int block, double tau, double t, const void* x, void* y, int m,
                                double tol, int max_substeps, bool reorth, bool two_pass, void* ws, cudaStream_t st);

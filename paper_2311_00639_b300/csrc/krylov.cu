@@ -35,6 +35,7 @@ void launch_tridiag(KScalars* sc, int m, double z_re, double z_im, double tol, c
 // Workspace layout (bytes, each region 256-aligned):
 //   KScalars | partialA [G] | partialN [G] | partialR [64][G][2] | vectors
 size_t krylov_ws_bytes(const syk_terms* h, int m, bool two_pass) {
+  if (!h->hermitian) return arnoldi_ws_bytes(h, m);
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t G = static_cast<size_t>(std::max(vec_grid(h), matvec_grid(h)));
   size_t b = up(sizeof(KScalars)) + 2 * up(G * sizeof(double)) + up(kMaxKrylov * G * 2 * sizeof(double));
@@ -46,6 +47,10 @@ size_t krylov_ws_bytes(const syk_terms* h, int m, bool two_pass) {
 // Evolve one state.  x and y are device vectors of D amplitudes; y may alias x.
 KrylovResult krylov_evolve_one(const syk_terms* h, int block, double tau, double t, const void* x, void* y, int m,
                                double tol, int max_substeps, bool reorth, bool two_pass, void* ws, cudaStream_t st) {
+  if (!h->hermitian) {  // complex couplings: full orthogonalisation (Arnoldi) instead of the three-term recurrence
+    SYK_REQUIRE(!reorth && !two_pass, "a non-Hermitian H needs the stored Arnoldi basis (no reorth / two_pass)");
+    return arnoldi_evolve_one(h, block, tau, t, x, y, m, tol, max_substeps, ws, st);
+  }
   KrylovResult res;
   auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t G = static_cast<size_t>(std::max(vec_grid(h), matvec_grid(h)));
@@ -58,7 +63,9 @@ KrylovResult krylov_evolve_one(const syk_terms* h, int block, double tau, double
   p += up(G * sizeof(double));
   double* partialR = reinterpret_cast<double*>(p);
   p += up(kMaxKrylov * G * 2 * sizeof(double));
-  const size_t vb = up(static_cast<size_t>(h->D) * elem_bytes(h->dtype));
+  // basis vectors back to back: the combine and re-orthogonalisation kernels
+  // index vector j at j * D amplitudes
+  const size_t vb = static_cast<size_t>(h->D) * elem_bytes(h->dtype);
   char* vecs = p;
   const size_t esz = elem_bytes(h->dtype);
   const int npA = matvec_grid(h), npN = vec_grid(h);

@@ -37,6 +37,7 @@ struct DevBuf {
 void otoc_run(const syk_terms* h, int a, int b, double beta, const double* tg, int n_t, int mode, int n_states,
               uint64_t seed, const void* psi_opt, int m, double tol, int max_sub, bool reorth, bool two_pass,
               double* F_raw, double* otoc, KrylovResult& tot, cudaStream_t st) {
+  SYK_REQUIRE(h->hermitian, "syk_otoc needs a Hermitian H (complex couplings: use syk_otoc_nonhermitian)");
   const size_t esz = elem_bytes(h->dtype);
   const size_t vb = (static_cast<size_t>(h->D) * esz + 255) & ~size_t(255);
   const bool exact = mode == SYK_OTOC_EXACT_TRACE;

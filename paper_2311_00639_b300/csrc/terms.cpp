@@ -148,6 +148,73 @@ void compile_terms(int N, int rep, int64_t T, const int32_t* quads, const double
   n_xgroups = static_cast<int64_t>(xs.size());
 }
 
+void compile_terms_complex(int N, int rep, int64_t T, const int32_t* quads, const double* J_re, const double* J_im,
+                           std::vector<BlockString>& out, int64_t& n_real, int64_t& n_xgroups) {
+  const int L = N / 2 - 1;
+  Pauli gam[64];
+  for (int n = 0; n < N; ++n) gam[n] = gamma_string(N, rep, n);
+  std::map<std::tuple<uint32_t, uint32_t, int>, size_t> index;
+  out.clear();
+  auto add = [&](uint32_t x, uint32_t z, bool imag, double cU, double cD) {
+    if (cU == 0.0 && cD == 0.0) return;
+    auto key = std::make_tuple(x, z, static_cast<int>(imag));
+    auto it = index.find(key);
+    if (it == index.end()) {
+      BlockString b;
+      b.x = x;
+      b.z = z;
+      b.imag = imag;
+      b.coef[0] = cU;
+      b.coef[1] = cD;
+      index.emplace(key, out.size());
+      out.push_back(b);
+    } else {
+      out[it->second].coef[0] += cU;
+      out[it->second].coef[1] += cD;
+    }
+  };
+  for (int64_t t = 0; t < T; ++t) {
+    const int32_t* q = quads + 4 * t;
+    for (int k = 0; k < 4; ++k)
+      SYK_REQUIRE(q[k] >= 0 && q[k] < N, "quad index out of range [0, N)");
+    SYK_REQUIRE(q[0] < q[1] && q[1] < q[2] && q[2] < q[3], "quad indices must be strictly increasing");
+    SYK_REQUIRE(std::isfinite(J_re[t]) && std::isfinite(J_im[t]), "non-finite coupling");
+    Pauli p = mul(mul(gam[q[0]], gam[q[1]]), mul(gam[q[2]], gam[q[3]]));
+    const uint64_t top = 1ull << L;
+    if (rep == SYK_REP_PAPER) {
+      SYK_REQUIRE((p.x & top) == 0, "internal: term leaves the parity block");
+    } else {
+      SYK_REQUIRE((popc(p.x) & 1) == 0, "internal: term changes parity");
+    }
+    uint32_t x, zeff;
+    int z_top;
+    fold_block(N, rep, p, x, zeff, z_top);
+    // value of the string in block form: 0.25 (J_re + i J_im) s_e s_fold (i if e is odd)
+    const bool odd = (p.e & 1) != 0;
+    const double s_e = (p.e == 0 || p.e == 1) ? 1.0 : -1.0;
+    const double s_fold = (popc(static_cast<uint64_t>(x) & zeff) & 1) ? -1.0 : 1.0;
+    const double g = 0.25 * s_e * s_fold;
+    const double v_re = odd ? -g * J_im[t] : g * J_re[t];  // (J_re + i J_im) * (odd ? i : 1)
+    const double v_im = odd ? g * J_re[t] : g * J_im[t];
+    const double sD = z_top ? -1.0 : 1.0;
+    add(x, zeff, false, v_re, sD * v_re);
+    add(x, zeff, true, v_im, sD * v_im);
+  }
+  out.erase(std::remove_if(out.begin(), out.end(),
+                           [](const BlockString& b) { return b.coef[0] == 0.0 && b.coef[1] == 0.0; }),
+            out.end());
+  std::sort(out.begin(), out.end(), [](const BlockString& a, const BlockString& b) {
+    return std::make_tuple(a.imag, a.x, a.z) < std::make_tuple(b.imag, b.x, b.z);
+  });
+  n_real = 0;
+  std::set<uint32_t> xs;
+  for (const auto& b : out) {
+    n_real += b.imag ? 0 : 1;
+    xs.insert(b.x);
+  }
+  n_xgroups = static_cast<int64_t>(xs.size());
+}
+
 ChiString compile_chi(int N, int rep, int n) {
   const Pauli g = gamma_string(N, rep, n);
   const int L = N / 2 - 1;

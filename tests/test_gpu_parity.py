@@ -435,3 +435,20 @@ def test_otoc_c64_vs_oracle_N16(syk):
         F, o, _ = h.otoc(N - 1, N - 2, 5.0, ts, psi=to_dev(psi, "c64"))
     ref = ot.F_state_blocks(N, "jw", HU, HD, X, N - 1, N - 2, 5.0, ts, *st)
     assert np.max(np.abs(F[0] - ref)) < 1e-4 * max(1.0, np.max(np.abs(ref)) * 4)
+
+
+@pytest.mark.parametrize("dtype,N", [("c64", 6), ("c64", 8), ("c64", 10), ("c128", 6), ("c128", 8)])
+def test_krylov_tiny_blocks(syk, dtype, N):
+    """Blocks of fewer than 256 bytes (D = 4..16): the stored Lanczos basis is
+    indexed at j * D amplitudes, whatever the workspace alignment."""
+    q, J, _ = si.sample_sparse_syk(N, 4, r=60 + N)
+    if len(J) < 2:
+        q, J = si.all_quads(N), np.random.default_rng(N).normal(size=len(si.all_quads(N)))
+    HU, HD = ham.blocks(ham.dense_H(N, q, J, "jw"), N, "jw")
+    lim = 1e-10 if dtype == "c128" else 5e-5
+    with syk.Terms(N, q, J, dtype=dtype) as h:
+        for blk, Hb in ((0, HU), (1, HD)):
+            x = rand_vec(Hb.shape[0], 70 + blk)
+            for z in (2.0j, 0.5 - 1.0j):
+                y, _ = h.krylov_evolve(to_dev(x, dtype), blk, z.real, z.imag)
+                assert rel_err(y.cpu().numpy(), dyn.evolve(Hb, z, x)) < lim, (dtype, N, blk, z)

@@ -163,6 +163,21 @@ def test_krylov_evolve_matches_eigh_and_expm_multiply():
         assert _rel(y.cpu().numpy(), ref) < 5e-5
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_krylov_tiny_chains(dtype, L):
+    """Vectors of fewer than 256 bytes: the stored Lanczos basis is indexed at
+    j * D amplitudes."""
+    import paper_2311_00639_b300 as syk
+
+    x, z, h = si.random_pauli_terms(L, 3 * L, seed=300 + L, max_weight=L)
+    Hd = spin.dense_H(L, x, z, h)
+    psi = _state(1 << L, 11)
+    with syk.PauliTerms(L, x, z, h, dtype=dtype) as t:
+        y, _ = t.krylov_evolve(_dev(psi, dtype), 0, 0.3, 2.0)
+        assert _rel(y.cpu().numpy(), dyn.evolve(Hd, 0.3 + 2.0j, psi)) < (1e-10 if dtype == "c128" else 5e-5)
+
+
 def test_pauli_otoc_same_state_and_philox_state_complex128():
     import paper_2311_00639_b300 as syk
 
