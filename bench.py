@@ -408,20 +408,23 @@ def spin_leg(args, syk, si, torch):
 
 # --------------------------------------------------------- non-Hermitian ----
 def nonherm_leg(args, syk, si, torch):
-    """Non-Hermitian sparse SYK (couplings J + iM, M drawn like J): H psi at
-    N = args.N (complex64, inputs resident; every term is a real-class and an
-    imaginary-class string) and infinite-temperature OTOC curves
-    (W(t) = e^{iH^dag t} W e^{-iHt}, a = N-1, b = N-2, t = 0..10 in 10
-    segments, one Philox state, Arnoldi) at N = 30, k = 3."""
+    """Non-Hermitian sparse SYK (couplings J + iM, M Gaussian with 0.1 the
+    spread of J: weakly non-Hermitian, so that the raw F, which grows like
+    e^{4 t max Im lambda}, stays readable): H psi at N = args.N (complex64,
+    inputs resident; every term is a real-class and an imaginary-class
+    string) and infinite-temperature OTOC curves (W(t) = e^{iH^dag t} W e^{-iHt},
+    a = N-1, b = N-2, t = 0..10 in 10 segments, one Philox state, Arnoldi) at
+    N = 30, k = 3."""
     import numpy as np
 
     def couplings(N, k, r):
         q, J, _ = si.sample_sparse_syk(N, k, r=r)
-        M = np.random.default_rng(900 + r).normal(size=len(J)) * math.sqrt(float(np.mean(J ** 2)))
+        M = 0.1 * np.random.default_rng(900 + r).normal(size=len(J)) * math.sqrt(float(np.mean(J ** 2)))
         return q, J, M
 
     q, J, M = couplings(args.N, args.k, 0)
-    out = {"workload": f"non-Hermitian sparse SYK N={args.N}, k={args.k:g}, couplings J + iM, one parity block"}
+    out = {"workload": f"non-Hermitian sparse SYK N={args.N}, k={args.k:g}, couplings J + iM (M ~ 0.1 J), "
+                       "one parity block"}
     with syk.Terms.complex(args.N, q, J, M, dtype="c64") as h:
         psi, _ = h.random_state(seed=1234, state_id=0, blocks=(0,))
         o = h.empty()
@@ -445,7 +448,7 @@ def nonherm_leg(args, syk, si, torch):
     diff = float(np.max(np.abs(curves["c64"]["F"] - curves["c128"]["F"])) / np.max(np.abs(curves["c128"]["F"])))
     for c in curves.values():
         c.pop("F")
-    out["otoc"] = {"workload": "N=30, k=3, couplings J + iM, a=29, b=28, beta=0, t=0..10 (11 points), one Philox "
+    out["otoc"] = {"workload": "N=30, k=3, couplings J + iM (M ~ 0.1 J), a=29, b=28, beta=0, t=0..10 (11 points), one Philox "
                                "state, Arnoldi (m=20 c64, m=30 c128)", **curves, "c64_vs_c128_max_rel_F_diff": diff}
     return out
 

@@ -80,9 +80,9 @@ def test_arnoldi_matches_expm_complex128(N):
                 ref = nh.evolve(Hs[blk], z, x)
                 assert _rel(y.cpu().numpy(), ref) < 1e-10, (N, blk, z)
                 assert st.matvecs > 0
-            # a small Krylov dimension forces several substeps
-            y, st = h.krylov_evolve(_dev(x, "c128"), blk, 0.0, 6.0, m=6)
-            assert st.substeps > 1
+            # a Krylov dimension below D forces several substeps (D <= m: one exact step)
+            y, st = h.krylov_evolve(_dev(x, "c128"), blk, 0.0, 6.0, m=12)
+            assert (st.substeps > 1) == (x.shape[0] > 12)
             assert _rel(y.cpu().numpy(), nh.evolve(Hs[blk], 6.0j, x)) < 1e-10
 
 
