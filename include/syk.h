@@ -179,6 +179,18 @@ typedef struct {
 int syk_plan_host(int N, int64_t T, const int32_t* quads, const double* J, int dtype, int rep,
                   size_t l2_budget_bytes, double straggler_ratio, int n_sm, syk_plan_host_out* out);
 /*
+ * syk_plan_strings_host — as syk_plan_host for an already compiled list of n
+ * block strings on L index bits (1 <= L <= 31; e.g. the output of
+ * syk_compile_pauli_host, with coef_U = coef_D = coef, or of
+ * syk_compile_terms_complex_host): x, z (below 2^L), coef_U, coef_D, imag
+ * are HOST arrays of n.  The plan, split and records are those
+ * syk_build_pauli_terms / syk_build_terms_complex upload for these strings.
+ * Errors: SYK_EINVAL.
+ */
+int syk_plan_strings_host(int L, int64_t n, const uint32_t* x, const uint32_t* z, const double* coef_U,
+                          const double* coef_D, const uint8_t* imag, int dtype, size_t l2_budget_bytes,
+                          double straggler_ratio, int n_sm, syk_plan_host_out* out);
+/*
  * Host-only: chi_n from block P as (chi psi)[m] = c_P (-1)^{popc(z & m)} psi[m ^ x]
  * in the other block; c_P = re[P] + i im[P] (arrays of 2).
  */

@@ -61,6 +61,7 @@ SIGNATURES = {
     "syk_compile_terms_host": (_I, [_I, _I64, _P, _P, _I, _I64, C.POINTER(_I64), _P, _P, _P, _P, _P]),
     "syk_compile_chi_host": (_I, [_I, _I, _I, _P, _P, _P, _P]),
     "syk_plan_host": (_I, [_I, _I64, _P, _P, _I, _I, _SZ, _D, _I, C.POINTER(PlanHostOut)]),
+    "syk_plan_strings_host": (_I, [_I, _I64, _P, _P, _P, _P, _P, _I, _SZ, _D, _I, C.POINTER(PlanHostOut)]),
     "syk_apply_H": (_I, [_P, _I, _P, _P, _I64, _P]),
     "syk_apply_chi": (_I, [_P, _I, _I, _P, _P, _I64, _P]),
     "syk_random_state": (_I, [_P, _U64, _U64, _P, _P, _P]),

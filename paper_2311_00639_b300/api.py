@@ -67,16 +67,10 @@ def compile_terms_host(N: int, quads, J, rep: str = "jw") -> dict:
     return out
 
 
-def plan_host(N: int, quads, J, dtype: str = "c64", rep: str = "jw", l2_budget_bytes: int = 0,
-              straggler_ratio: float = 0.0, n_sm: int = 148) -> dict:
-    """Host-only (no GPU): the matvec pass plan and complex64 record layout that
-    Terms(...) followed by replan(l2_budget_bytes, straggler_ratio) would use."""
-    lib = L.load()
-    q, j = _host_arrays(quads, J)
-    args = (N, q.shape[0], q.ctypes.data, j.ctypes.data, _DT[dtype], _REP[rep], l2_budget_bytes,
-            float(straggler_ratio), n_sm)
+def _plan_outputs(call) -> dict:
+    """Run a syk_plan_*_host call twice (sizes, then arrays) and unpack it."""
     o = L.PlanHostOut()
-    L.check(lib.syk_plan_host(*args, C.byref(o)))
+    L.check(call(C.byref(o)))
     n, P = o.n_terms, o.n_passes
     passes = (L.PassInfo * max(P, 1))()
     out = {"x": np.zeros(n, np.uint32), "z": np.zeros(n, np.uint32), "coef_U": np.zeros(n), "coef_D": np.zeros(n),
@@ -84,12 +78,39 @@ def plan_host(N: int, quads, J, dtype: str = "c64", rep: str = "jw", l2_budget_b
            "records": np.zeros((2, n + 1, 4), np.uint32)}
     o = L.PlanHostOut(term_capacity=n, pass_capacity=P, passes=C.cast(passes, C.c_void_p),
                       **{k: v.ctypes.data for k, v in out.items()})
-    L.check(lib.syk_plan_host(*args, C.byref(o)))
+    L.check(call(C.byref(o)))
     out["n_runs"] = o.n_runs
     out["passes"] = [{"t0": p.t0, "ti": p.ti, "t1": p.t1, "emask": p.emask, "cls": list(p.cls),
                       "split_chunks": p.split_chunks, "split_terms": p.split_terms,
                       "dep": np.array([list(p.dep[b]) for b in range(3)], np.uint32)} for p in passes[:P]]
     return out
+
+
+def plan_host(N: int, quads, J, dtype: str = "c64", rep: str = "jw", l2_budget_bytes: int = 0,
+              straggler_ratio: float = 0.0, n_sm: int = 148) -> dict:
+    """Host-only (no GPU): the matvec pass plan and complex64 record layout that
+    Terms(...) followed by replan(l2_budget_bytes, straggler_ratio) would use."""
+    lib = L.load()
+    q, j = _host_arrays(quads, J)
+    return _plan_outputs(lambda o: lib.syk_plan_host(N, q.shape[0], q.ctypes.data, j.ctypes.data, _DT[dtype],
+                                                     _REP[rep], l2_budget_bytes, float(straggler_ratio), n_sm, o))
+
+
+def plan_strings_host(L_bits: int, strings: dict, dtype: str = "c64", l2_budget_bytes: int = 0,
+                      straggler_ratio: float = 0.0, n_sm: int = 148) -> dict:
+    """Host-only (no GPU): the plan and records for compiled strings on L_bits
+    index bits, e.g. compile_pauli_host(...) (coef used for both blocks) or
+    compile_terms_complex_host(...)."""
+    lib = L.load()
+    x = np.ascontiguousarray(strings["x"], dtype=np.uint32)
+    z = np.ascontiguousarray(strings["z"], dtype=np.uint32)
+    cu = np.ascontiguousarray(strings.get("coef_U", strings.get("coef")), dtype=np.float64)
+    cd = np.ascontiguousarray(strings.get("coef_D", strings.get("coef")), dtype=np.float64)
+    im = np.ascontiguousarray(strings["imag"], dtype=np.uint8)
+    return _plan_outputs(lambda o: lib.syk_plan_strings_host(L_bits, len(x), x.ctypes.data, z.ctypes.data,
+                                                             cu.ctypes.data, cd.ctypes.data, im.ctypes.data,
+                                                             _DT[dtype], l2_budget_bytes, float(straggler_ratio),
+                                                             n_sm, o))
 
 
 def _pauli_arrays(x, z, h):

@@ -12,6 +12,7 @@
 #include <tuple>
 #include <vector>
 
+#include "entry.h"
 #include "kernels.cuh"
 
 namespace syk {
@@ -290,60 +291,14 @@ int syk_compile_terms_host(int N, int64_t T, const int32_t* quads, const double*
 int syk_plan_host(int N, int64_t T, const int32_t* quads, const double* J, int dtype, int rep,
                   size_t l2_budget_bytes, double straggler_ratio, int n_sm, syk_plan_host_out* out) {
   return guarded("syk_plan_host", [&] {
-    SYK_REQUIRE(out != nullptr, "null output");
     SYK_REQUIRE(N >= 4 && N <= 64 && N % 2 == 0, "N must be even and in [4, 64]");
     SYK_REQUIRE(T >= 0 && T <= (int64_t(1) << 31) - 1, "T out of range");
     SYK_REQUIRE(T == 0 || (quads && J), "null quads or J");
-    SYK_REQUIRE(dtype == SYK_C64 || dtype == SYK_C128, "dtype must be SYK_C64 or SYK_C128");
     SYK_REQUIRE(rep == SYK_REP_JW || rep == SYK_REP_PAPER, "rep must be SYK_REP_JW or SYK_REP_PAPER");
-    SYK_REQUIRE(l2_budget_bytes == 0 || l2_budget_bytes >= 4096, "l2_budget_bytes must be 0 or >= 4096");
-    SYK_REQUIRE(std::isfinite(straggler_ratio) && straggler_ratio >= 0, "straggler_ratio must be >= 0");
-    SYK_REQUIRE(n_sm >= 1, "n_sm must be >= 1");
-    SYK_REQUIRE(out->term_capacity >= 0 && out->pass_capacity >= 0, "negative capacity");
-    if (l2_budget_bytes == 0) {
-      l2_budget_bytes = syk::default_l2_budget(dtype);
-      straggler_ratio = syk::default_hbm_ratio(dtype);
-    }
-    syk_terms h;  // host fields only: nothing is allocated on a device
-    h.N = N;
-    h.L = N / 2 - 1;
-    h.D = int64_t(1) << h.L;
-    h.dtype = dtype;
-    h.rep = rep;
-    h.n_sm = n_sm;
-    syk::compile_terms(N, rep, T, quads, J, h.terms, h.n_real, h.n_xgroups);
-    h.passes = syk::plan_passes(h.terms, h.L, syk::elem_bytes(dtype), l2_budget_bytes, straggler_ratio);
-    syk::plan_split(&h);
-    std::vector<syk::TermF> rec[2];
-    const size_t n = h.terms.size();
-    out->n_runs = syk::build_records(h.terms, h.passes, rec);
-    out->n_terms = static_cast<int64_t>(n);
-    out->n_passes = static_cast<int64_t>(h.passes.size());
-    if (out->term_capacity < out->n_terms || out->pass_capacity < out->n_passes) return;
-    for (size_t p = 0; p < h.passes.size() && out->passes; ++p) {
-      const syk::PassPlan& ps = h.passes[p];
-      syk_pass_info& o = out->passes[p];
-      o.t0 = ps.t0;
-      o.ti = ps.ti;
-      o.t1 = ps.t1;
-      o.emask = ps.emask;
-      for (int c = 0; c < 9; ++c) o.cls[c] = ps.cls[c];
-      o.split_chunks = h.split_chunks[p];
-      o.split_terms = h.split_terms[p];
-      std::memcpy(o.dep, ps.dep, sizeof(o.dep));
-    }
-    for (size_t i = 0; i < n; ++i) {
-      const auto& t = h.terms[i];
-      if (out->x) out->x[i] = t.x;
-      if (out->z) out->z[i] = t.z;
-      if (out->coef_U) out->coef_U[i] = t.coef[0];
-      if (out->coef_D) out->coef_D[i] = t.coef[1];
-      if (out->imag) out->imag[i] = t.imag ? 1 : 0;
-      if (out->straggler) out->straggler[i] = t.straggler ? 1 : 0;
-    }
-    if (out->records)
-      for (int b = 0; b < 2; ++b)
-        std::memcpy(out->records + static_cast<size_t>(b) * (n + 1) * 4, rec[b].data(), (n + 1) * sizeof(syk::TermF));
+    std::vector<syk::BlockString> terms;
+    int64_t n_real = 0, n_x = 0;
+    syk::compile_terms(N, rep, T, quads, J, terms, n_real, n_x);
+    syk::plan_view(std::move(terms), N / 2 - 1, dtype, l2_budget_bytes, straggler_ratio, n_sm, out);
   });
 }
 

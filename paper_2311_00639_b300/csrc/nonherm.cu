@@ -20,64 +20,17 @@
 #include <string>
 #include <vector>
 
+#include "entry.h"
 #include "kernels.cuh"
 
 namespace syk {
 namespace {
-
-template <typename F>
-int guarded_nh(const char* fn, F&& f) {
-  try {
-    f();
-    return SYK_OK;
-  } catch (const Error& e) {
-    set_last_error(std::string(fn) + ": " + e.what());
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    set_last_error(std::string(fn) + ": host allocation failed");
-    return SYK_ENOMEM;
-  } catch (const std::exception& e) {
-    set_last_error(std::string(fn) + ": " + e.what());
-    return SYK_EINVAL;
-  } catch (...) {
-    set_last_error(std::string(fn) + ": unknown failure");
-    return SYK_EINVAL;
-  }
-}
 
 void check_args(int N, int64_t T, const int32_t* quads, const double* J_re, const double* J_im, int rep) {
   SYK_REQUIRE(N >= 4 && N <= 64 && N % 2 == 0, "N must be even and in [4, 64]");
   SYK_REQUIRE(T >= 0 && T <= (int64_t(1) << 31) - 1, "T out of range");
   SYK_REQUIRE(T == 0 || (quads && J_re && J_im), "null quads, J_re or J_im");
   SYK_REQUIRE(rep == SYK_REP_JW || rep == SYK_REP_PAPER, "rep must be SYK_REP_JW or SYK_REP_PAPER");
-}
-
-// A handle for `terms` on the current device: syk_build_terms with no terms
-// (device, chi strings, empty table), then the strings and a re-plan.
-syk_terms_t* make_handle(int N_build, int dtype, int rep, std::vector<BlockString>&& terms, int64_t n_input,
-                         int64_t n_real, int64_t n_x, bool hermitian) {
-  syk_terms_t* raw = nullptr;
-  int rc = syk_build_terms(N_build, 0, nullptr, nullptr, dtype, rep, &raw);
-  if (rc != SYK_OK) {
-    char buf[512];
-    syk_last_error(buf, sizeof buf);
-    throw Error(rc, buf);
-  }
-  raw->terms = std::move(terms);
-  raw->n_input = n_input;
-  raw->n_real = n_real;
-  raw->n_xgroups = n_x;
-  raw->hermitian = hermitian;
-  raw->sum_abs = 0.0;
-  for (const auto& t : raw->terms) raw->sum_abs += std::max(std::fabs(t.coef[0]), std::fabs(t.coef[1]));
-  rc = syk_terms_replan(raw, 0, 0.0);
-  if (rc != SYK_OK) {
-    char buf[512];
-    syk_last_error(buf, sizeof buf);
-    syk_terms_destroy(raw);
-    throw Error(rc, buf);
-  }
-  return raw;
 }
 
 struct HandleGuard {
@@ -209,7 +162,7 @@ extern "C" {
 int syk_compile_terms_complex_host(int N, int64_t T, const int32_t* quads, const double* J_re, const double* J_im,
                                    int rep, int64_t capacity, int64_t* n_terms, uint32_t* x, uint32_t* z,
                                    double* coef_U, double* coef_D, uint8_t* imag) {
-  return syk::guarded_nh("syk_compile_terms_complex_host", [&] {
+  return syk::guard_call("syk_compile_terms_complex_host", [&] {
     syk::check_args(N, T, quads, J_re, J_im, rep);
     SYK_REQUIRE(n_terms != nullptr, "null n_terms");
     SYK_REQUIRE(capacity >= 0, "negative capacity");
@@ -230,7 +183,7 @@ int syk_compile_terms_complex_host(int N, int64_t T, const int32_t* quads, const
 
 int syk_build_terms_complex(int N, int64_t T, const int32_t* quads, const double* J_re, const double* J_im, int dtype,
                             int rep, syk_terms_t** out) {
-  return syk::guarded_nh("syk_build_terms_complex", [&] {
+  return syk::guard_call("syk_build_terms_complex", [&] {
     SYK_REQUIRE(out != nullptr, "null output handle pointer");
     *out = nullptr;
     syk::check_args(N, T, quads, J_re, J_im, rep);
@@ -245,14 +198,14 @@ int syk_build_terms_complex(int N, int64_t T, const int32_t* quads, const double
 }
 
 int syk_terms_is_hermitian(const syk_terms_t* h, int* hermitian) {
-  return syk::guarded_nh("syk_terms_is_hermitian", [&] {
+  return syk::guard_call("syk_terms_is_hermitian", [&] {
     SYK_REQUIRE(h && hermitian, "null argument");
     *hermitian = h->hermitian ? 1 : 0;
   });
 }
 
 int syk_terms_adjoint(const syk_terms_t* h, syk_terms_t** out) {
-  return syk::guarded_nh("syk_terms_adjoint", [&] {
+  return syk::guard_call("syk_terms_adjoint", [&] {
     SYK_REQUIRE(h && out, "null argument");
     *out = nullptr;
     int dev = -1;
@@ -265,7 +218,7 @@ int syk_terms_adjoint(const syk_terms_t* h, syk_terms_t** out) {
 int syk_otoc_nonhermitian(const syk_terms_t* h, int a, int b, const double* t_grid, int n_t, int mode, int n_states,
                           uint64_t seed, const void* psi_opt, const syk_krylov_params* p, double* F_raw, double* otoc,
                           syk_krylov_stats* stats, syk_stream_t stream) {
-  return syk::guarded_nh("syk_otoc_nonhermitian", [&] {
+  return syk::guard_call("syk_otoc_nonhermitian", [&] {
     SYK_REQUIRE(h != nullptr, "null terms handle");
     int dev = -1;
     SYK_CUDA(cudaGetDevice(&dev));

@@ -12,11 +12,11 @@
 //   (P psi)[m] = i^k (-1)^{popc(z & (m ^ x))} psi[m ^ x]
 //              = (-i)^k (-1)^{popc(z & m)} psi[m ^ x].
 //
-// A Pauli handle is an ordinary handle: syk_build_terms with no terms on
-// N = 2L + 2 (so D = 2^L), then given the compiled strings and re-planned by
-// syk_terms_replan, which builds and uploads the pass plan and records.  It
-// holds no Majoranas (N = 0), so the Majorana entry points refuse it, and its
-// two block slots carry the same coefficients; every call here uses block 0.
+// A Pauli handle is an ordinary handle (make_handle: syk_build_terms with no
+// terms on N = 2L + 2, so D = 2^L, then the compiled strings and a re-plan
+// that builds and uploads the pass plan and records).  It holds no Majoranas
+// (N = 0), so the Majorana entry points refuse it, and its two block slots
+// carry the same coefficients; every call here uses block 0.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,30 +29,11 @@
 #include <vector>
 
 #include "device_common.cuh"
+#include "entry.h"
 #include "kernels.cuh"
 
 namespace syk {
 namespace {
-
-template <typename F>
-int guarded_spin(const char* fn, F&& f) {
-  try {
-    f();
-    return SYK_OK;
-  } catch (const Error& e) {
-    set_last_error(std::string(fn) + ": " + e.what());
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    set_last_error(std::string(fn) + ": host allocation failed");
-    return SYK_ENOMEM;
-  } catch (const std::exception& e) {
-    set_last_error(std::string(fn) + ": " + e.what());
-    return SYK_EINVAL;
-  } catch (...) {
-    set_last_error(std::string(fn) + ": unknown failure");
-    return SYK_EINVAL;
-  }
-}
 
 uint32_t qubit_mask(int L) { return L >= 32 ? 0xFFFFFFFFu : ((1u << L) - 1u); }
 
@@ -64,7 +45,7 @@ void string_phase(uint32_t x, uint32_t z, bool& imag, double& sign) {
 }
 
 void compile_pauli(int L, int64_t T, const uint32_t* x, const uint32_t* z, const double* h,
-                   std::vector<BlockString>& out, int64_t& n_real, int64_t& n_xgroups, double& sum_abs) {
+                   std::vector<BlockString>& out, int64_t& n_real, int64_t& n_xgroups) {
   SYK_REQUIRE(L >= 1 && L <= 31, "n_qubits must be in [1, 31]");
   SYK_REQUIRE(T >= 0 && T <= (int64_t(1) << 31) - 1, "T out of range");
   SYK_REQUIRE(T == 0 || (x && z && h), "null x, z or h");
@@ -99,11 +80,9 @@ void compile_pauli(int L, int64_t T, const uint32_t* x, const uint32_t* z, const
     return std::make_tuple(a.imag, a.x, a.z) < std::make_tuple(b.imag, b.x, b.z);
   });
   n_real = 0;
-  sum_abs = 0.0;
   std::set<uint32_t> xs;
   for (const auto& b : out) {
     n_real += b.imag ? 0 : 1;
-    sum_abs += std::fabs(b.coef[0]);
     xs.insert(b.x);
   }
   n_xgroups = static_cast<int64_t>(xs.size());
@@ -273,13 +252,12 @@ extern "C" {
 int syk_compile_pauli_host(int n_qubits, int64_t T, const uint32_t* x, const uint32_t* z, const double* h,
                            int64_t capacity, int64_t* n_terms, uint32_t* x_out, uint32_t* z_out, double* coef,
                            uint8_t* imag) {
-  return syk::guarded_spin("syk_compile_pauli_host", [&] {
+  return syk::guard_call("syk_compile_pauli_host", [&] {
     SYK_REQUIRE(n_terms != nullptr, "null n_terms");
     SYK_REQUIRE(capacity >= 0, "negative capacity");
     std::vector<syk::BlockString> terms;
     int64_t n_real = 0, n_x = 0;
-    double sum_abs = 0.0;
-    syk::compile_pauli(n_qubits, T, x, z, h, terms, n_real, n_x, sum_abs);
+    syk::compile_pauli(n_qubits, T, x, z, h, terms, n_real, n_x);
     *n_terms = static_cast<int64_t>(terms.size());
     const int64_t n = std::min<int64_t>(capacity, *n_terms);
     for (int64_t i = 0; i < n; ++i) {
@@ -293,43 +271,24 @@ int syk_compile_pauli_host(int n_qubits, int64_t T, const uint32_t* x, const uin
 
 int syk_build_pauli_terms(int n_qubits, int64_t T, const uint32_t* x, const uint32_t* z, const double* h,
                           int dtype, syk_terms_t** out) {
-  return syk::guarded_spin("syk_build_pauli_terms", [&] {
+  return syk::guard_call("syk_build_pauli_terms", [&] {
     SYK_REQUIRE(out != nullptr, "null output handle pointer");
     *out = nullptr;
     SYK_REQUIRE(dtype == SYK_C64 || dtype == SYK_C128, "dtype must be SYK_C64 or SYK_C128");
     std::vector<syk::BlockString> terms;
     int64_t n_real = 0, n_x = 0;
-    double sum_abs = 0.0;
-    syk::compile_pauli(n_qubits, T, x, z, h, terms, n_real, n_x, sum_abs);
-    syk_terms_t* raw = nullptr;
-    const int N = 2 * n_qubits + 2;  // D = 2^{N/2 - 1} = 2^n_qubits
-    int rc = syk_build_terms(N, 0, nullptr, nullptr, dtype, SYK_REP_JW, &raw);
-    if (rc != SYK_OK) {
-      char buf[512];
-      syk_last_error(buf, sizeof buf);
-      throw syk::Error(rc, buf);
-    }
-    raw->terms = std::move(terms);
+    syk::compile_pauli(n_qubits, T, x, z, h, terms, n_real, n_x);
+    // N = 2 n_qubits + 2 Majoranas give D = 2^{N/2 - 1} = 2^n_qubits amplitudes
+    syk_terms_t* raw = syk::make_handle(2 * n_qubits + 2, dtype, SYK_REP_JW, std::move(terms), T, n_real, n_x, true);
     raw->N = 0;  // no Majoranas: the chi / OTOC / batch entry points refuse the handle
     raw->rep = SYK_REP_PAULI;
-    raw->n_input = T;
-    raw->n_real = n_real;
-    raw->n_xgroups = n_x;
-    raw->sum_abs = sum_abs;
-    rc = syk_terms_replan(raw, 0, 0.0);  // default plan of the dtype; builds and uploads the table
-    if (rc != SYK_OK) {
-      char buf[512];
-      syk_last_error(buf, sizeof buf);
-      syk_terms_destroy(raw);
-      throw syk::Error(rc, buf);
-    }
     *out = raw;
   });
 }
 
 int syk_apply_pauli(const syk_terms_t* h, uint32_t x, uint32_t z, const void* psi, void* out, int64_t nstates,
                     syk_stream_t stream) {
-  return syk::guarded_spin("syk_apply_pauli", [&] {
+  return syk::guard_call("syk_apply_pauli", [&] {
     syk::check_pauli_handle(h);
     const uint32_t lim = syk::qubit_mask(h->L);
     SYK_REQUIRE((x & ~lim) == 0 && (z & ~lim) == 0, "Pauli string acts on a qubit >= n_qubits");
@@ -347,7 +306,7 @@ int syk_pauli_otoc(const syk_terms_t* h, uint32_t w_x, uint32_t w_z, uint32_t v_
                    const double* t_grid, int n_t, int mode, int n_states, uint64_t seed, const void* psi_opt,
                    const syk_krylov_params* p, double* F_raw, double* otoc, syk_krylov_stats* stats,
                    syk_stream_t stream) {
-  return syk::guarded_spin("syk_pauli_otoc", [&] {
+  return syk::guard_call("syk_pauli_otoc", [&] {
     syk::check_pauli_handle(h);
     const uint32_t lim = syk::qubit_mask(h->L);
     SYK_REQUIRE(((w_x | w_z | v_x | v_z) & ~lim) == 0, "Pauli string acts on a qubit >= n_qubits");

@@ -13,7 +13,10 @@ plain sum over terms), so these tests check, without a GPU, that
 * the records carry exactly the plan's terms, runs, flags and sign bits, and
   H psi evaluated from the records alone equals the oracle's block
   Hamiltonian applied to psi (to the records' float32 coefficient rounding);
-* split passes cover their terms with non-empty chunks.
+* split passes cover their terms with non-empty chunks;
+* the same holds for the compiled string tables of spin chains and of
+  complex couplings (syk_plan_strings_host), and the benchmark's L=31 chain
+  gets the plan its ncu summary describes.
 """
 import os
 
@@ -247,3 +250,84 @@ def test_plan_host_rejects_bad_arguments(pkg):
         pkg.plan_host(20, q, J, "c64", "jw", 0, 0.0, 0)
     empty = pkg.plan_host(20, np.zeros((0, 4), np.int32), np.zeros(0), "c64")
     assert len(empty["x"]) == 0 and len(empty["passes"]) == 1 and empty["n_runs"] == 0
+
+
+def _records_apply(records, n, psi):
+    """H psi from one block's records alone (masked masks, float32 coefficient, imag flag)."""
+    D = len(psi)
+    m = np.arange(D, dtype=np.int64)
+    x, z, c, fl = unpack(records[:n])
+    out = np.zeros(D, dtype=np.complex128)
+    for xt, zt, ct, ft in zip(x.tolist(), z.tolist(), c.tolist(), fl.tolist()):
+        sign = 1.0 - 2.0 * (np.bitwise_count(m & zt) & 1)
+        out += (1j * ct if (ft >> 3) & 1 else ct) * sign * psi[m ^ xt]
+    return out, np.abs(c).sum()
+
+
+@pytest.mark.parametrize("L,budget,ratio", [(16, 1 << 14, 0.0), (16, 1 << 15, 3.0), (14, 0, 0.0)])
+def test_plan_strings_spin_chain_records_reproduce_oracle(pkg, L, budget, ratio):
+    """The host plan view of a Pauli-string table (syk_plan_strings_host): a
+    partition of the compiled strings, and records that alone apply the
+    oracle's spin Hamiltonian."""
+    from oracle import spin
+
+    x, z, h, _ = si.heisenberg_chain(L, W=2.0, r=7)
+    x2, z2, h2 = si.random_pauli_terms(L, 30, seed=9, max_weight=4)
+    x, z, h = np.concatenate([x, x2]), np.concatenate([z, z2]), np.concatenate([h, h2])
+    comp = pkg.compile_pauli_host(L, x, z, h)
+    plan = pkg.plan_strings_host(L, comp, "c64", budget, ratio)
+    n = len(comp["x"])
+    key = lambda xs, zs, cs, ims: sorted(zip(xs.tolist(), zs.tolist(), cs.tolist(), ims.tolist()))
+    assert key(plan["x"], plan["z"], plan["coef_U"], plan["imag"]) == key(comp["x"], comp["z"], comp["coef"],
+                                                                         comp["imag"])
+    assert np.array_equal(plan["coef_U"], plan["coef_D"])
+    if budget:
+        assert len(plan["passes"]) >= 2
+    psi = np.random.default_rng(L).normal(size=1 << L) + 0j
+    ref = spin.csr_H(L, x, z, h) @ psi
+    for blk in (0, 1):
+        out, s = _records_apply(plan["records"][blk], n, psi)
+        assert np.max(np.abs(out - ref)) <= 2.0 ** -24 * s * np.abs(psi).max() * 1.01 + 1e-12
+
+
+def test_plan_strings_complex_couplings_records_reproduce_oracle(pkg):
+    """Non-Hermitian SYK (complex couplings): real- and imaginary-class strings
+    with equal masks share runs; the records alone apply the oracle's blocks."""
+    from oracle import nonherm as nh
+
+    N = 28
+    q, J, _ = si.sample_sparse_syk(N, 4, r=5)
+    M = np.random.default_rng(5).normal(size=len(J)) * np.sqrt(np.mean(J ** 2))
+    comp = pkg.compile_terms_complex_host(N, q, J, M, "jw")
+    plan = pkg.plan_strings_host(N // 2 - 1, comp, "c64", 8192, 3.0)
+    n = len(comp["x"])
+    assert n == 2 * len(J)  # every term: a real and an imaginary string
+    assert plan["n_runs"] <= len(np.unique(comp["x"] >> TILE_BITS)) * len(plan["passes"])
+    psi = np.random.default_rng(1).normal(size=1 << (N // 2 - 1)) + 1j
+    for blk in (0, 1):
+        out, s = _records_apply(plan["records"][blk], n, psi)
+        ref = nh.csr_block(N, q, J, M, "jw", blk) @ psi
+        assert np.max(np.abs(out - ref)) <= 2.0 ** -24 * s * np.abs(psi).max() * 1.01 + 1e-12
+
+
+def test_default_heisenberg_L31_plan(pkg):
+    """The default complex64 plan of the benchmark's chain (L=31, W=5, 124
+    strings): 2 passes of 104 and 20 strings, 12 + 10 staged tiles per output
+    tile, as in the ncu summary of that workload."""
+    x, z, h, _ = si.heisenberg_chain(31, 5.0, r=0)
+    plan = pkg.plan_strings_host(31, pkg.compile_pauli_host(31, x, z, h), "c64")
+    assert [p["t1"] - p["t0"] for p in plan["passes"]] == [104, 20]
+    assert plan["n_runs"] == 22 and not plan["straggler"].any()
+
+
+def test_plan_strings_rejects_bad_arguments(pkg):
+    from paper_2311_00639_b300 import SykError
+
+    comp = {"x": np.array([1 << 5], np.uint32), "z": np.zeros(1, np.uint32), "coef": np.ones(1),
+            "imag": np.zeros(1, np.uint8)}
+    with pytest.raises(SykError):
+        pkg.plan_strings_host(5, comp)  # bit 5 of a 5-bit index
+    with pytest.raises(SykError):
+        pkg.plan_strings_host(0, comp)
+    comp["x"][0] = 1
+    assert len(pkg.plan_strings_host(5, comp)["x"]) == 1
