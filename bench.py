@@ -434,6 +434,8 @@ def nonherm_leg(args, syk, si, torch):
                            "note": "rate counts input terms (quads); each compiles to two strings"}
         del psi, o
     torch.cuda.empty_cache()
+    if args.no_otoc:
+        return out
     grid = np.linspace(0.0, 10.0, 11)
     q, J, M = couplings(30, 3.0, 1)
     curves = {}
