@@ -42,66 +42,90 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 
 // partial[(i * G + b) * 2 + {0, 1}] = (Re, Im) of sum over block b's amplitudes
-// of conj(V_i) w, for i < nvec (G = gridDim.x).
+// of conj(V_i) w, for i < nvec (G = gridDim.x, blockDim.x = 256).  Eight basis
+// vectors per pass over w; the 16 sums of a pass are reduced together (warp
+// shuffles, then one barrier and a fixed-order sum over the 8 warps).
 template <typename Real>
-__global__ void k_arn_dots(const typename CT<Real>::T* __restrict__ V, const typename CT<Real>::T* __restrict__ w,
-                           uint64_t D, int nvec, double* partial, const KScalars* sc, int j) {
+__global__ void __launch_bounds__(256) k_arn_dots(const typename CT<Real>::T* __restrict__ V,
+                                                  const typename CT<Real>::T* __restrict__ w, uint64_t D, int nvec,
+                                                  double* partial, const KScalars* sc, int j) {
   using C = typename CT<Real>::T;
+  __shared__ double red[8][16];
   if (sc->m_eff <= j) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i0 = 0; i0 < nvec; i0 += 8) {
     const int nb = min(8, nvec - i0);
-    double ar[8], ai[8];
+    double acc[16];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) ar[q] = ai[q] = 0.0;
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
     for (uint64_t k = blockIdx.x * 256ull + threadIdx.x; k < D; k += gridDim.x * 256ull) {
       const C ww = w[k];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         if (q < nb) {
           const C v = V[static_cast<uint64_t>(i0 + q) * D + k];
-          ar[q] += static_cast<double>(v.x) * ww.x + static_cast<double>(v.y) * ww.y;
-          ai[q] += static_cast<double>(v.x) * ww.y - static_cast<double>(v.y) * ww.x;
+          acc[2 * q] += static_cast<double>(v.x) * ww.x + static_cast<double>(v.y) * ww.y;
+          acc[2 * q + 1] += static_cast<double>(v.x) * ww.y - static_cast<double>(v.y) * ww.x;
         }
       }
     }
-    for (int q = 0; q < nb; ++q) {
-      const double sr = block_sum(ar[q]);
-      const double si = block_sum(ai[q]);
-      if (threadIdx.x == 0) {
-        partial[(static_cast<uint64_t>(i0 + q) * gridDim.x + blockIdx.x) * 2] = sr;
-        partial[(static_cast<uint64_t>(i0 + q) * gridDim.x + blockIdx.x) * 2 + 1] = si;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const double v = warp_sum(acc[q]);
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * nb) {
+      double t = 0.0;
+      for (int wi = 0; wi < 8; ++wi) t += red[wi][threadIdx.x];
+      partial[(static_cast<uint64_t>(i0 + (threadIdx.x >> 1)) * gridDim.x + blockIdx.x) * 2 + (threadIdx.x & 1)] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// h_i = sum over the G dot partials of vector i (one warp per (i, Re/Im)
+// pair, fixed order): written to hbuf and added to the Hessenberg column
+// (the two Gram-Schmidt passes accumulate).  One block of 256 threads.
+__global__ void __launch_bounds__(256) k_arn_reduce(const double* partial, int G, int nvec, double2* hcol,
+                                                    double2* hbuf, const KScalars* sc, int j) {
+  if (sc->m_eff <= j) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int pr = warp; pr < 2 * nvec; pr += 8) {
+    const int i = pr >> 1, comp = pr & 1;
+    double t = 0.0;
+    for (int b = lane; b < G; b += 32) t += partial[(static_cast<uint64_t>(i) * G + b) * 2 + comp];
+    t = warp_sum(t);
+    if (lane == 0) {
+      if (comp) {
+        hbuf[i].y = t;
+        hcol[i].y += t;
+      } else {
+        hbuf[i].x = t;
+        hcol[i].x += t;
       }
     }
   }
 }
 
-// h_i = sum of the dot partials; hcol[i] += h_i (block 0); w -= sum_i h_i V_i;
-// partialN[b] = sum |w|^2.  Every block reduces the partials in the same order.
+// w -= sum_i h_i V_i with h from k_arn_reduce; partialN[b] = sum |w|^2.
 template <typename Real>
 __global__ void k_arn_sub(typename CT<Real>::T* w, const typename CT<Real>::T* __restrict__ V, uint64_t D, int nvec,
-                          const double* partial, double2* hcol, double* partialN, const KScalars* sc, int j) {
+                          const double2* hbuf, double* partialN, const KScalars* sc, int j) {
   using C = typename CT<Real>::T;
   if (sc->m_eff <= j) return;
-  __shared__ double hr[kMaxKrylov], hi[kMaxKrylov];
-  for (int i = 0; i < nvec; ++i) {
-    const double a = sum_partials(partial + static_cast<uint64_t>(i) * gridDim.x * 2, gridDim.x, 2);
-    const double b = sum_partials(partial + static_cast<uint64_t>(i) * gridDim.x * 2 + 1, gridDim.x, 2);
-    if (threadIdx.x == 0) {
-      hr[i] = a;
-      hi[i] = b;
-    }
+  __shared__ Real hr[kMaxKrylov], hi[kMaxKrylov];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    hr[i] = static_cast<Real>(hbuf[i].x);
+    hi[i] = static_cast<Real>(hbuf[i].y);
   }
   __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x < nvec) {
-    hcol[threadIdx.x].x += hr[threadIdx.x];
-    hcol[threadIdx.x].y += hi[threadIdx.x];
-  }
   double s = 0.0;
   for (uint64_t k = blockIdx.x * 256ull + threadIdx.x; k < D; k += gridDim.x * 256ull) {
     C ww = w[k];
     for (int i = 0; i < nvec; ++i) {
       const C v = V[static_cast<uint64_t>(i) * D + k];
-      const Real a = static_cast<Real>(hr[i]), b = static_cast<Real>(hi[i]);
+      const Real a = hr[i], b = hi[i];
       ww.x = fma_(-a, v.x, fma_(b, v.y, ww.x));
       ww.y = fma_(-a, v.y, fma_(-b, v.x, ww.y));
     }
@@ -373,11 +397,13 @@ size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 }  // namespace
 
 // Workspace: KScalars | dot partials [kMaxKrylov][G][2] | norm partials [G] |
-// Hessenberg kLd x kLd | Pade scratch kExpmMats x kLd x kLd | m + 1 vectors.
+// Hessenberg kLd x kLd | projection coefficients kLd | Pade scratch
+// kExpmMats x kLd x kLd | m + 1 vectors.
 size_t arnoldi_ws_bytes(const syk_terms* h, int m) {
   const size_t G = static_cast<size_t>(vec_grid(h));
   size_t b = up256(sizeof(KScalars)) + up256(kMaxKrylov * G * 2 * sizeof(double)) + up256(G * sizeof(double));
-  b += up256(kLd * kLd * sizeof(double2)) + up256(static_cast<size_t>(kExpmMats) * kLd * kLd * sizeof(double2));
+  b += up256(kLd * kLd * sizeof(double2)) + up256(kLd * sizeof(double2)) +
+       up256(static_cast<size_t>(kExpmMats) * kLd * kLd * sizeof(double2));
   b += up256((static_cast<size_t>(m) + 1) * static_cast<size_t>(h->D) * elem_bytes(h->dtype));
   return b;
 }
@@ -395,6 +421,8 @@ KrylovResult arnoldi_evolve_one(const syk_terms* h, int block, double tau, doubl
   p += up256(G * sizeof(double));
   double2* hess = reinterpret_cast<double2*>(p);
   p += up256(kLd * kLd * sizeof(double2));
+  double2* hbuf = reinterpret_cast<double2*>(p);
+  p += up256(kLd * sizeof(double2));
   double2* scratch = reinterpret_cast<double2*>(p);
   p += up256(static_cast<size_t>(kExpmMats) * kLd * kLd * sizeof(double2));
   const size_t esz = elem_bytes(h->dtype);
@@ -426,8 +454,8 @@ KrylovResult arnoldi_evolve_one(const syk_terms* h, int block, double tau, doubl
         const C* Vb = static_cast<const C*>(V(0));
         for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
           k_arn_dots<Real><<<Gi, 256, 0, st>>>(Vb, w, h->D, j + 1, partialD, sc, j);
-          k_arn_sub<Real><<<Gi, 256, 0, st>>>(w, Vb, h->D, j + 1, partialD, hess + static_cast<size_t>(j) * kLd,
-                                             partialN, sc, j);
+          k_arn_reduce<<<1, 256, 0, st>>>(partialD, Gi, j + 1, hess + static_cast<size_t>(j) * kLd, hbuf, sc, j);
+          k_arn_sub<Real><<<Gi, 256, 0, st>>>(w, Vb, h->D, j + 1, hbuf, partialN, sc, j);
         }
         k_arn_next<Real><<<Gi, 256, 0, st>>>(w, h->D, partialN, Gi, hess + static_cast<size_t>(j) * kLd + j + 1, sc,
                                             j, brk);
