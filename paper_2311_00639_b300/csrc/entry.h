@@ -3,9 +3,12 @@
 // construction from an already compiled list of block strings.
 #pragma once
 
+#include <cmath>
 #include <new>
 #include <string>
 #include <vector>
+
+#include <cuda_runtime.h>
 
 #include "internal.h"
 
@@ -31,6 +34,46 @@ int guard_call(const char* fn, F&& f) {
     set_last_error(std::string(fn) + ": unknown failure");
     return SYK_EINVAL;
   }
+}
+
+// Device memory owned for the duration of one call.
+struct DeviceBuffer {
+  void* p = nullptr;
+  explicit DeviceBuffer(size_t n) {
+    if (n && cudaMalloc(&p, n) != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Error(SYK_ENOMEM, "device allocation of " + std::to_string(n) + " bytes failed");
+    }
+  }
+  ~DeviceBuffer() {
+    if (p) cudaFree(p);
+  }
+  DeviceBuffer(const DeviceBuffer&) = delete;
+  DeviceBuffer& operator=(const DeviceBuffer&) = delete;
+};
+
+// syk_krylov_params with the library defaults filled in (zero fields:
+// m = 20 for complex64 / 30 for complex128, tol = 1e-6 / 1e-12, 1000
+// substeps), validated.
+struct KrylovSettings {
+  int m;
+  double tol;
+  int max_sub;
+  bool reorth, two_pass;
+};
+inline KrylovSettings krylov_settings(int dtype, const syk_krylov_params* p) {
+  KrylovSettings k;
+  k.m = (p && p->m) ? p->m : default_krylov_m(dtype);
+  k.tol = (p && p->tol > 0) ? p->tol : (dtype == SYK_C128 ? 1e-12 : 1e-6);
+  k.max_sub = (p && p->max_substeps) ? p->max_substeps : 1000;
+  k.reorth = p && p->reorth;
+  k.two_pass = p && p->two_pass;
+  SYK_REQUIRE(k.m >= 1 && k.m <= kMaxKrylov, "Krylov dimension m must be in [1, 64]");
+  SYK_REQUIRE(std::isfinite(k.tol) && k.tol > 0, "tol must be positive");
+  SYK_REQUIRE(k.max_sub >= 1, "max_substeps must be >= 1");
+  SYK_REQUIRE(!(k.reorth && k.two_pass), "reorth and two_pass cannot be combined");
+  return k;
 }
 
 // A handle on the current device holding `terms`: syk_build_terms with no

@@ -40,22 +40,6 @@ struct HandleGuard {
   }
 };
 
-struct DevMem {
-  void* p = nullptr;
-  explicit DevMem(size_t n) {
-    if (n && cudaMalloc(&p, n) != cudaSuccess) {
-      p = nullptr;
-      cudaGetLastError();
-      throw Error(SYK_ENOMEM, "device allocation of " + std::to_string(n) + " bytes failed");
-    }
-  }
-  ~DevMem() {
-    if (p) cudaFree(p);
-  }
-  DevMem(const DevMem&) = delete;
-  DevMem& operator=(const DevMem&) = delete;
-};
-
 syk_terms_t* build_adjoint(const syk_terms* h) {
   std::vector<BlockString> terms = h->terms;
   for (auto& t : terms) {
@@ -83,9 +67,9 @@ void otoc_nh_run(const syk_terms* h, const syk_terms* hd, int a, int b, const do
   const bool exact = mode == SYK_OTOC_EXACT_TRACE;
   const int rows = exact ? 1 : n_states;
   const int G = vec_grid(h);
-  DevMem vecs(4 * vb);
-  DevMem ws(std::max(krylov_ws_bytes(h, m, false), krylov_ws_bytes(hd, m, false)));
-  DevMem small((2 * static_cast<size_t>(G) + 8) * sizeof(double) + static_cast<size_t>(rows) * n_t * 2 * sizeof(double));
+  DeviceBuffer vecs(4 * vb);
+  DeviceBuffer ws(std::max(krylov_ws_bytes(h, m, false), krylov_ws_bytes(hd, m, false)));
+  DeviceBuffer small((2 * static_cast<size_t>(G) + 8) * sizeof(double) + static_cast<size_t>(rows) * n_t * 2 * sizeof(double));
   char* vp = static_cast<char*>(vecs.p);
   void* u0 = vp;
   void* bra = vp + vb;
@@ -232,17 +216,13 @@ int syk_otoc_nonhermitian(const syk_terms_t* h, int a, int b, const double* t_gr
     SYK_REQUIRE(mode == SYK_OTOC_TYPICAL || mode == SYK_OTOC_EXACT_TRACE, "bad mode");
     if (mode == SYK_OTOC_TYPICAL) SYK_REQUIRE(n_states >= 1, "n_states must be >= 1");
     if (psi_opt) SYK_REQUIRE((reinterpret_cast<uintptr_t>(psi_opt) & 15) == 0, "psi_opt not 16-byte aligned");
-    const int m = (p && p->m) ? p->m : syk::default_krylov_m(h->dtype);
-    const double tol = (p && p->tol > 0) ? p->tol : (h->dtype == SYK_C128 ? 1e-12 : 1e-6);
-    const int max_sub = (p && p->max_substeps) ? p->max_substeps : 1000;
-    SYK_REQUIRE(m >= 1 && m <= syk::kMaxKrylov, "Krylov dimension m must be in [1, 64]");
-    SYK_REQUIRE(std::isfinite(tol) && tol > 0 && max_sub >= 1, "bad tol or max_substeps");
-    SYK_REQUIRE(!(p && (p->reorth || p->two_pass)), "reorth and two_pass are not available here");
+    const syk::KrylovSettings k = syk::krylov_settings(h->dtype, p);
+    SYK_REQUIRE(!k.reorth && !k.two_pass, "reorth and two_pass are not available here");
     syk::HandleGuard adj;
     adj.h = syk::build_adjoint(h);
     syk::KrylovResult tot;
-    syk::otoc_nh_run(h, adj.h, a, b, t_grid, n_t, mode, n_states, seed, psi_opt, m, tol, max_sub, F_raw, otoc, tot,
-                     reinterpret_cast<cudaStream_t>(stream));
+    syk::otoc_nh_run(h, adj.h, a, b, t_grid, n_t, mode, n_states, seed, psi_opt, k.m, k.tol, k.max_sub, F_raw, otoc,
+                     tot, reinterpret_cast<cudaStream_t>(stream));
     if (stats) {
       stats->matvecs = tot.matvecs;
       stats->substeps = tot.substeps;

@@ -147,22 +147,6 @@ void launch_pauli(const syk_terms* h, uint32_t x, uint32_t z, const void* psi, v
   SYK_CUDA(cudaGetLastError());
 }
 
-struct DeviceBuffer {
-  void* p = nullptr;
-  explicit DeviceBuffer(size_t n) {
-    if (n && cudaMalloc(&p, n) != cudaSuccess) {
-      p = nullptr;
-      cudaGetLastError();
-      throw Error(SYK_ENOMEM, "device allocation of " + std::to_string(n) + " bytes failed");
-    }
-  }
-  ~DeviceBuffer() {
-    if (p) cudaFree(p);
-  }
-  DeviceBuffer(const DeviceBuffer&) = delete;
-  DeviceBuffer& operator=(const DeviceBuffer&) = delete;
-};
-
 // The single-state chain of Eq. (2) with W, V for each state (or basis state),
 // on the handle's one state space (block 0):
 //   u0  = e^{-bH/8} psi                     (once per state),
@@ -319,17 +303,10 @@ int syk_pauli_otoc(const syk_terms_t* h, uint32_t w_x, uint32_t w_z, uint32_t v_
     SYK_REQUIRE(mode == SYK_OTOC_TYPICAL || mode == SYK_OTOC_EXACT_TRACE, "bad mode");
     if (mode == SYK_OTOC_TYPICAL) SYK_REQUIRE(n_states >= 1, "n_states must be >= 1");
     if (psi_opt) syk::check_ptr(psi_opt, "psi_opt");
-    const int m = (p && p->m) ? p->m : syk::default_krylov_m(h->dtype);
-    const double tol = (p && p->tol > 0) ? p->tol : (h->dtype == SYK_C128 ? 1e-12 : 1e-6);
-    const int max_sub = (p && p->max_substeps) ? p->max_substeps : 1000;
-    const bool reorth = p && p->reorth, two_pass = p && p->two_pass;
-    SYK_REQUIRE(m >= 1 && m <= syk::kMaxKrylov, "Krylov dimension m must be in [1, 64]");
-    SYK_REQUIRE(std::isfinite(tol) && tol > 0, "tol must be positive");
-    SYK_REQUIRE(max_sub >= 1, "max_substeps must be >= 1");
-    SYK_REQUIRE(!(reorth && two_pass), "reorth and two_pass cannot be combined");
+    const syk::KrylovSettings k = syk::krylov_settings(h->dtype, p);
     syk::KrylovResult tot;
-    syk::pauli_otoc_run(h, w_x, w_z, v_x, v_z, beta, t_grid, n_t, mode, n_states, seed, psi_opt, m, tol, max_sub,
-                        reorth, two_pass, F_raw, otoc, tot, reinterpret_cast<cudaStream_t>(stream));
+    syk::pauli_otoc_run(h, w_x, w_z, v_x, v_z, beta, t_grid, n_t, mode, n_states, seed, psi_opt, k.m, k.tol,
+                        k.max_sub, k.reorth, k.two_pass, F_raw, otoc, tot, reinterpret_cast<cudaStream_t>(stream));
     if (stats) {
       stats->matvecs = tot.matvecs;
       stats->substeps = tot.substeps;
