@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-l2", action="store_true")
     ap.add_argument("--no-otoc", action="store_true", help="skip the batched / served OTOC legs")
+    ap.add_argument("--no-outlook", action="store_true",
+                    help="skip the spin-chain and non-Hermitian H psi keys of the benchmark line")
     ap.add_argument("--n64-m", type=int, default=10, help="Krylov dimension of the N=64 end-to-end OTOC")
     ap.add_argument("--n64-two-pass", action="store_true",
                     help="N=64 OTOC: regenerate the Krylov basis in a second pass (3 vectors) instead of storing "
@@ -327,6 +329,45 @@ def oracle_spin_rows_rate(L, W, seconds=10.0, seed=77):
     return len(h) * nrows / dt / 1e9, nrows, len(h)
 
 
+def hpsi_rate(t, steps, warmup, torch, n_input=None):
+    """Time `steps` H psi of handle t (block 0, one resident Philox state);
+    the rate counts n_input terms per amplitude (default: the compiled strings)."""
+    psi, _ = t.random_state(seed=1234, state_id=0, blocks=(0,))
+    o = t.empty()
+    dt = time_matvecs(t, psi, o, steps, warmup, torch)
+    del psi, o
+    torch.cuda.empty_cache()
+    n = t.n_terms if n_input is None else n_input
+    return {"Gtermamp_s": n * t.D * steps / dt / 1e9, "ms_per_Hpsi": dt * 1e3 / steps, "terms": n,
+            "strings": t.n_terms, "passes": t.info["n_passes"], "tile_reads": t.info["n_tile_reads"], "steps": steps}
+
+
+def outlook_hpsi(args, syk, si, torch):
+    """Informational keys of the benchmark line: H psi of the outlook's two
+    models at the benchmark's scale (complex64, 2^31 amplitudes): the
+    random-field Heisenberg chain (L=31, W=5, 124 strings) and the N=64, k=4
+    quadruples with complex couplings J + iM (M ~ 0.1 J, 522 strings).  A
+    failure here is recorded in place of the numbers and never stops the line."""
+    import numpy as np
+
+    out = {}
+    steps = max(1, min(5, args.steps))
+    try:
+        x, z, h, _ = si.heisenberg_chain(31, 5.0, r=0)
+        with syk.PauliTerms(31, x, z, h, dtype="c64") as t:
+            out["spin_chain_L31"] = hpsi_rate(t, steps, 2, torch)
+    except Exception as e:  # informational only
+        out["spin_chain_L31"] = {"error": str(e)[:300]}
+    try:
+        q, J, _ = si.sample_sparse_syk(64, 4.0, r=0)
+        M = 0.1 * np.random.default_rng(900).normal(size=len(J)) * math.sqrt(float(np.mean(J ** 2)))
+        with syk.Terms.complex(64, q, J, M, dtype="c64") as t:
+            out["nonhermitian_N64"] = hpsi_rate(t, steps, 2, torch, n_input=len(J))
+    except Exception as e:  # informational only
+        out["nonhermitian_N64"] = {"error": str(e)[:300]}
+    return out
+
+
 def spin_leg(args, syk, si, torch):
     """The outlook's spin chains: the random-field Heisenberg chain
     H = sum S_i.S_{i+1} - sum h_i S^z_i (periodic, W = 5) as Pauli strings.
@@ -347,18 +388,11 @@ def spin_leg(args, syk, si, torch):
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     for dtype, steps in (("c64", args.steps), ("c128", max(1, min(3, args.steps)))):
         with syk.PauliTerms(L, x, z, h, dtype=dtype) as t:
-            psi, _ = t.random_state(seed=1234, state_id=0, blocks=(0,))
-            o = t.empty()
             if dtype == "c64":
                 clocks.start()
-            dt = time_matvecs(t, psi, o, steps, args.warmup if dtype == "c64" else 1, torch)
+            out[dtype] = hpsi_rate(t, steps, args.warmup if dtype == "c64" else 1, torch)
             if dtype == "c64":
                 out["clocks"] = clocks.stop()
-            out[dtype] = {"Gtermamp_s": t.n_terms * t.D * steps / dt / 1e9, "ms_per_Hpsi": dt * 1e3 / steps,
-                          "terms": t.n_terms, "passes": t.info["n_passes"], "tile_reads": t.info["n_tile_reads"],
-                          "steps": steps}
-            del psi, o
-        torch.cuda.empty_cache()
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     peaks = {}
     try:
@@ -426,14 +460,8 @@ def nonherm_leg(args, syk, si, torch):
     out = {"workload": f"non-Hermitian sparse SYK N={args.N}, k={args.k:g}, couplings J + iM (M ~ 0.1 J), "
                        "one parity block"}
     with syk.Terms.complex(args.N, q, J, M, dtype="c64") as h:
-        psi, _ = h.random_state(seed=1234, state_id=0, blocks=(0,))
-        o = h.empty()
-        dt = time_matvecs(h, psi, o, args.steps, args.warmup, torch)
-        out["Hpsi_c64"] = {"Gtermamp_s": len(J) * h.D * args.steps / dt / 1e9, "ms_per_Hpsi": dt * 1e3 / args.steps,
-                           "quads": len(J), "strings": h.n_terms, "passes": h.info["n_passes"],
-                           "note": "rate counts input terms (quads); each compiles to two strings"}
-        del psi, o
-    torch.cuda.empty_cache()
+        out["Hpsi_c64"] = dict(hpsi_rate(h, args.steps, args.warmup, torch, n_input=len(J)),
+                               note="rate counts input terms (quads); each compiles to two strings")
     if args.no_otoc:
         return out
     grid = np.linspace(0.0, 10.0, 11)
@@ -652,6 +680,10 @@ def ours(args):
             "frac_of_l2_resident": staged_gbps / l2res["staged_GBps"] if l2res else None}
     roof["traffic"] = measured_traffic(T, D)
 
+    outlook = None
+    if rank == 0 and not args.no_outlook:
+        outlook = outlook_hpsi(args, syk, si, torch)
+
     batched = served = None
     if not args.no_otoc:
         torch.cuda.empty_cache()
@@ -672,7 +704,8 @@ def ours(args):
                 "config": {**workload_config(args, T), "parallelism": f"replicas x{world}",
                            "matvec_passes": h.info["n_passes"]},
                 "gpu_launches": args.steps * h.info["n_passes"], "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "fp64": fp64, "clocks": clk, "gpu": props.name, "otoc_batched": batched, "otoc_served": served}
+                "fp64": fp64, "clocks": clk, "gpu": props.name, "otoc_batched": batched, "otoc_served": served,
+                "outlook_hpsi": outlook}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
