@@ -3,7 +3,7 @@ limit reduces to the beta = 0 OTOC of Eq. (2); the adjoint of a complex
 coupling sum is the conjugate-coupling sum; a single complex term has a
 closed-form exponential; when every term anticommutes with chi_a and chi_b the
 OTOC chain collapses to a product of evolutions with no Majorana left; the
-trace is the mean over basis states."""
+trace is the mean over basis states, and typical states estimate it."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -116,3 +116,20 @@ def test_trace_is_mean_over_basis_and_t0_value():
     acc = sum(nh.F_state(H, X, N - 1, N - 2, ts, e) for e in np.eye(H.shape[0]))
     assert np.allclose(Ft, acc / H.shape[0], atol=1e-13)
     assert np.isclose(Ft[0], -0.25, atol=1e-14)  # chi_a chi_b chi_a chi_b = -1/4 at t = 0
+
+
+def test_typical_states_estimate_the_trace():
+    """As for the Hermitian OTOC: the mean over normalised complex-Gaussian
+    states approaches the exact trace within O(|F| / sqrt(S dim))."""
+    N = 10
+    q, J, M = _instance(N, r=6)
+    H = nh.dense_H(N, q, J, 0.3 * M, "jw")
+    X = mj.chis(N, "jw")
+    ts = [0.0, 0.8]
+    Ft = nh.F_trace(H, X, N - 1, N - 2, ts)
+    S = 200
+    rng = np.random.default_rng(13)
+    acc = np.zeros(len(ts), dtype=np.complex128)
+    for _ in range(S):
+        acc += nh.F_state(H, X, N - 1, N - 2, ts, _normed(rng.normal(size=H.shape[0]) + 1j * rng.normal(size=H.shape[0])))
+    assert np.all(np.abs(acc / S - Ft) < 6.0 * np.max(np.abs(Ft)) / np.sqrt(S * H.shape[0]))

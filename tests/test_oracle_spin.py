@@ -205,3 +205,20 @@ def test_otoc_trace_t0_beta0_and_mean_over_basis():
     acc = sum(otoc.F_state(H, {0: W0, 1: V2}, 0, 1, 3.0, ts, e) for e in np.eye(1 << L))
     assert np.allclose(Ft, acc / (1 << L), atol=1e-13)
     assert np.max(np.abs(Ft.imag)) < 1e-13
+
+
+def test_typical_states_estimate_the_trace():
+    """The mean of F_psi over normalised complex-Gaussian states approaches
+    the exact trace within the statistical error O(1 / sqrt(S dim))."""
+    L = 6
+    x, z, h, _ = si.heisenberg_chain(L, W=1.0, r=2)
+    H = spin.dense_H(L, x, z, h)
+    X = {0: spin.pauli_dense(L, *si.pauli_mask({0: "Z"})), 1: spin.pauli_dense(L, *si.pauli_mask({3: "Z"}))}
+    ts = np.array([0.0, 1.0, 2.0])
+    Ft = otoc.F_trace(H, X, 0, 1, 0.0, ts)
+    S = 300
+    rng = np.random.default_rng(12)
+    acc = np.zeros(len(ts), dtype=np.complex128)
+    for _ in range(S):
+        acc += otoc.F_state(H, X, 0, 1, 0.0, ts, _normed(rng.normal(size=1 << L) + 1j * rng.normal(size=1 << L)))
+    assert np.all(np.abs(acc / S - Ft) < 4.0 / math.sqrt(S * (1 << L)))
