@@ -37,6 +37,7 @@ __all__ = [
     "all_quads",
     "sample_sparse_syk",
     "sample_dense_syk",
+    "sample_commuting_syk",
     "random_state",
     "philox4x32_10",
     "philox_state",
@@ -75,6 +76,29 @@ def sample_dense_syk(N: int, seed: int = 0, J0: float = 1.0):
     quads = all_quads(N)
     J = rng.normal(0.0, math.sqrt(6.0 * J0 * J0 / N ** 3), size=quads.shape[0])
     return quads, J, 1.0
+
+
+def sample_commuting_syk(N: int, seed: int, n_terms: int | None = None, J0: float = 0.5):
+    """Quadruples that pairwise share 0 or 2 indices, so that their products
+    commute (the oracle's exact commuting tier).
+
+    The N Majorana indices are split into N/2 pairs: (N-2, N-1) (the
+    Majoranas of the paper's OTOC, so that their OTOC varies with t) and a
+    random perfect matching of the rest; each term is the union of two
+    distinct pairs, for n_terms distinct random pairs of pairs (default N),
+    written as a sorted quadruple; J ~ N(0, J0^2) (couplings of order one, so
+    that a few dozen terms spread the spectrum over a few units).  Returns
+    (quads int32 [T, 4], J float64 [T], pairs int32 [N/2, 2]).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rest = np.sort(rng.permutation(N - 2).reshape(-1, 2), axis=1)
+    pairs = np.concatenate([rest, [[N - 2, N - 1]]])
+    edges = [(i, j) for i in range(len(pairs)) for j in range(i + 1, len(pairs))]
+    T = min(len(edges), N if n_terms is None else n_terms)
+    pick = rng.choice(len(edges), size=T, replace=False)
+    quads = np.array([np.sort(np.concatenate([pairs[edges[e][0]], pairs[edges[e][1]]])) for e in pick])
+    J = rng.normal(0.0, J0, size=T)
+    return quads.astype(np.int32).reshape(-1, 4), J.astype(np.float64), pairs.astype(np.int32)
 
 
 def random_state(N: int, seed: int, dtype=np.complex128):

@@ -366,3 +366,66 @@ def test_green_block_form_equals_full_space(rep):
         # G(0) = <psi|e^{-bH}|psi>/2 for any H (chi_a^2 = 1/2)
         psi = mj.to_full(pU, pD, N, rep)
         assert np.isclose(full[0], 0.5 * np.vdot(psi, sla.expm(-beta * H) @ psi), atol=1e-13)
+
+
+# --- Commuting-term tier (exact evolution by a product of single-term exponentials)
+COMMUTING_QUADS = np.array([[0, 3, 5, 9], [1, 2, 6, 11], [4, 7, 8, 10], [0, 1, 2, 3]], dtype=np.int32)
+
+
+def test_commuting_quads_really_commute():
+    """The pin set: the fourth quadruple shares two indices with each of the
+    first two and none with the third, so all dense products commute."""
+    from oracle import commuting as cm
+
+    N = 12
+    X = mj.chis(N, "jw")
+    P = [X[i] @ X[j] @ X[k] @ X[l] for i, j, k, l in COMMUTING_QUADS]
+    for A in P:
+        assert np.allclose(A @ A, np.eye(A.shape[0]) / 16.0, atol=1e-14)
+        for B in P:
+            assert np.allclose(A @ B, B @ A, atol=1e-14)
+    cm.check_commuting(COMMUTING_QUADS)
+    with pytest.raises(ValueError):
+        cm.check_commuting(np.array([[0, 1, 2, 3], [0, 4, 5, 6]]))
+
+
+@pytest.mark.parametrize("rep", REPS)
+def test_commuting_evolve_matches_dense_eigh(rep):
+    """e^{-zH} as a product of cosh - 4 sinh P factors equals the dense
+    eigendecomposition e^{-zH} (a library routine) for complex z, both blocks:
+    the fixed set above (terms split at their two lowest indices), and a
+    matching-generated set whose terms are split along the matching's pairs
+    (odd permutations included, so the reordering sign matters)."""
+    from oracle import commuting as cm
+
+    N = 12
+    q2, J2, pairs = si.sample_commuting_syk(N, seed=5, n_terms=12)
+    cases = [(COMMUTING_QUADS, np.array([0.9, -1.3, 0.4, 1.7]), None), (q2, J2, pairs)]
+    assert any(cm._split_pairs(q, pairs)[2] < 0 for q in q2)
+    v = np.random.default_rng(3).normal(size=1 << 5) + 1j * np.random.default_rng(4).normal(size=1 << 5)
+    for quads, J, pr in cases:
+        HU, HD = ham.blocks(ham.dense_H(N, quads, J, rep), N, rep)
+        for blk, Hb in ((0, HU), (1, HD)):
+            for z in (0.7, 2.5j, 1.2 - 3.0j):
+                ref = dyn.evolve(Hb, z, v)
+                got = cm.evolve(N, rep, quads, J, blk, z, v, pr)
+                assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_commuting_otoc_matches_dense_block_formula():
+    """The commuting-tier OTOC equals the dense parity-block OTOC (eigh) at
+    N=12, on a matching-generated term set (F varies with t)."""
+    from oracle import commuting as cm
+
+    N = 12
+    quads, J, pairs = si.sample_commuting_syk(N, seed=6, n_terms=10)
+    H = ham.dense_H(N, quads, J, "jw")
+    HU, HD = ham.blocks(H, N, "jw")
+    X = mj.chis(N, "jw")
+    pU, pD = si.random_state(N, seed=21)
+    ts = [0.0, 0.8, 2.5]
+    for a, b in ((N - 1, N - 2), (3, 8)):
+        ref = otoc.F_state_blocks(N, "jw", HU, HD, X, a, b, 3.0, ts, pU, pD)
+        got = cm.F_state(N, "jw", quads, J, a, b, 3.0, ts, pU, pD, pairs)
+        assert np.max(np.abs(got - ref)) < 1e-12
+        assert np.max(np.abs(ref - ref[0])) > 1e-3

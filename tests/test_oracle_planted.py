@@ -16,6 +16,7 @@ import textwrap
 import numpy as np
 import pytest
 
+from oracle import commuting as cm
 from oracle import majorana as mj
 from oracle import nonherm as nh
 from oracle import otoc
@@ -75,6 +76,14 @@ SOURCE_MUTATIONS = [
      [(TS.test_xx_chain_free_fermion_spectrum, {}), (TS.test_two_site_heisenberg_singlet_triplet, {})]),
     ("non-Hermitian chain without the adjoint", nh, "_chain", "Ub = sla.expm(1j * t * H.conj().T)",
      "Ub = sla.expm(1j * t * H)", [(TN.test_otoc_closed_form_all_terms_contain_a_and_b, {})]),
+    ("commuting factor sinh sign", cm, "evolve", "np.cosh(w) * out - 4.0 * np.sinh(w)",
+     "np.cosh(w) * out + 4.0 * np.sinh(w)", [(T0.test_commuting_evolve_matches_dense_eigh, {"rep": "jw"})]),
+    ("commuting factor with J/2", cm, "evolve", "w = z * c / 4.0", "w = z * c / 2.0",
+     [(T0.test_commuting_evolve_matches_dense_eigh, {"rep": "jw"})]),
+    ("commuting pair reordering sign dropped", cm, "_split_pairs", "return (a, b), (c, d), (-1) ** inversions",
+     "return (a, b), (c, d), 1", [(T0.test_commuting_evolve_matches_dense_eigh, {"rep": "jw"})]),
+    ("commuting OTOC ket without its last Majorana", cm, "F_state", "k = ca @ k", "k = k",
+     [(T0.test_commuting_otoc_matches_dense_block_formula, {})]),
     ("non-Hermitian couplings conjugated", nh, "couplings",
      "np.asarray(J_re, dtype=np.float64) + 1j * np.asarray(J_im, dtype=np.float64)",
      "np.asarray(J_re, dtype=np.float64) - 1j * np.asarray(J_im, dtype=np.float64)",
