@@ -268,8 +268,8 @@ int syk_krylov_evolve(const syk_terms_t* h, int block, double tau, double t, con
  * another framework's memory pool which already owns the device memory, or a
  * service whose device footprint must stay fixed after start-up.  It takes
  * no workspace argument and allocates nothing; its workspace is a static
- * device array of 16 MiB inside the library, held on every GPU that loads
- * the library until the process exits.  The paper has no counterpart to this
+ * device array of 16 MiB inside the library, held on every GPU where it has
+ * been called (see the first-call rule below) until the process exits.  The paper has no counterpart to this
  * call.
  *   * A call whose workspace (syk_krylov_workspace_bytes with the same
  *     params) exceeds 16 MiB returns SYK_EINVAL without queuing work.
@@ -277,8 +277,16 @@ int syk_krylov_evolve(const syk_terms_t* h, int block, double tau, double t, con
  *     calls that overlap on the GPU (other streams, other host threads) race
  *     and corrupt each other's results: serialise them.
  *   * The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, once per device); make that first call before
- *     any stream capture.
+ *     (cudaGetSymbolAddress, once per device).  CUDA loads the library's
+ *     device code lazily, so that first call is also when the 16 MiB are
+ *     reserved on the device: it does take device memory.  Callers that must
+ *     not allocate later make one warm-up call at start-up, before any
+ *     stream capture: tau = t = 0 reserves the array (it only copies x to
+ *     y); a real evolve of the kind they will run also loads its kernels.
+ *     Later calls allocate nothing.
+ *   * The address is cached for the device context current at the first
+ *     call; like every handle, it does not survive cudaDeviceReset or a
+ *     re-created primary context.
  * Arguments, aliasing, synchronisation and errors are as for
  * syk_krylov_evolve.
  */
@@ -478,6 +486,8 @@ typedef struct {
                                 full space (exact trace = sum of these jobs over g, divided by 2D) */
   int kind;                  /* SYK_JOB_OTOC, or SYK_JOB_GREEN: G(t) = <psi| e^{(it-b/2)H} chi_a
                                 e^{-iHt} chi_a e^{-bH/2} |psi> (supplement, Green function; b unused) */
+  double* otoc_out;          /* HOST [n_t], optional: the job's normalised curve Re F(t) / Re F(0)
+                                (Re G(t) / Re G(0) for SYK_JOB_GREEN), written when it finishes */
 } syk_otoc_job;
 enum { SYK_JOB_OTOC = 0, SYK_JOB_GREEN = 1 };
 /* max_bytes: device arena for job state (allocated once); max_slots: jobs in flight;
@@ -500,6 +510,29 @@ int syk_batch_info(const syk_batch_t* batch, int* live_jobs, size_t* bytes_in_us
 size_t syk_batch_job_bytes(const syk_batch_t* batch, const syk_terms_t* h, int n_t);
 
 /*
+ * syk_otoc_exact_trace_batched — the exact-trace OTOC of Eq. (2) for several
+ * Majorana pairs through the batched engine: for each pair (a, b),
+ *   F_tr(t) = sum_g F_{e_g}(t) / 2D  over the 2D basis states e_g of both
+ *   parity blocks (one batched job per (pair, g), as syk_otoc_job with
+ *   basis_index = g),  OTOC(t) = Re F_tr(t) / Re F_tr(0).
+ *   pairs    : HOST int32 [n_pairs][2] (a, b).
+ *   t_grid   : HOST double [n_t], non-decreasing.
+ *   max_slots, max_bytes, p : as for syk_batch_create (jobs live at once,
+ *              device arena, Krylov parameters; two_pass / reorth refused).
+ *   F_out    : HOST double [n_pairs][n_t][2] (re, im of F_tr), may be NULL.
+ *   otoc_out : HOST double [n_pairs][n_t], may be NULL.
+ *   stats    : HOST, optional: matvecs and substeps summed over all jobs.
+ * The sum over g runs in the fixed order g = 0, 1, ..., 2D-1 in FP64 on the
+ * host, whatever order the jobs finish in, so results are reproducible.
+ * Blocking; creates and destroys its own batch.  Errors: SYK_EINVAL,
+ * SYK_ENOMEM, SYK_ENOCONV (a job did not converge), SYK_ETIMEOUT, SYK_ECUDA.
+ */
+int syk_otoc_exact_trace_batched(const syk_terms_t* h, int n_pairs, const int32_t* pairs, double beta,
+                                 const double* t_grid, int n_t, int max_slots, size_t max_bytes,
+                                 const syk_krylov_params* p, double* F_out, double* otoc_out,
+                                 syk_krylov_stats* stats);
+
+/*
  * syk_bounded_wait_selftest — failure-detection self-test (no paper
  * counterpart): one CTA waits, with the bounded wait of the TMA pipelines, on
  * an mbarrier that nothing completes.  Returns SYK_ETIMEOUT after the wait
@@ -508,6 +541,29 @@ size_t syk_batch_job_bytes(const syk_batch_t* batch, const syk_terms_t* h, int n
  * `stream`.
  */
 int syk_bounded_wait_selftest(syk_stream_t stream);
+
+/*
+ * Hardware probes for the benchmark's roofline denominators (no paper
+ * counterpart; the hot path never calls them).  Both synchronise `stream`.
+ *
+ * syk_probe_staging — bytes per second moved from `buf` (DEVICE, `bytes`
+ * long, 16-byte aligned, at least 16 KiB; make it smaller than L2 to measure
+ * L2 -> shared memory) by the complex64 matvec's pipeline shape: 16 KiB bulk
+ * copies (cp.async.bulk + mbarrier), 3 stages, one producer lane and 4
+ * consumer warps per CTA, 4 CTAs per SM, `jobs_per_cta` tiles per CTA on a
+ * scattered walk over the buffer.  reads = 0: the consumers only wait for and
+ * release each stage; 1 or 2: they also read every staged tile that many
+ * times from shared memory (16-byte loads); -1: no shared memory, the same
+ * tiles read with 16-byte global loads that do not allocate in L1.  The rate
+ * counts the tile bytes fetched from `buf` once per job.  One warm-up launch,
+ * then one timed launch (CUDA events).  Errors: SYK_EINVAL, SYK_ENOMEM,
+ * SYK_ETIMEOUT (a bounded wait expired), SYK_ECUDA.
+ */
+int syk_probe_staging(const void* buf, size_t bytes, int reads, int jobs_per_cta, double* bytes_per_s,
+                      syk_stream_t stream);
+/* syk_probe_fp64 — FP64 fused multiply-adds per second of the whole GPU
+ * (8 independent chains per thread, 8 CTAs of 256 threads per SM). */
+int syk_probe_fp64(double* dfma_per_s, syk_stream_t stream);
 
 /* Message of the last failing call on this thread (always NUL-terminated). */
 int syk_last_error(char* buf, size_t n);

@@ -33,7 +33,7 @@ class OtocJob(C.Structure):
     _fields_ = [("h", C.c_void_p), ("a", C.c_int), ("b", C.c_int), ("beta", C.c_double), ("t_grid", C.c_void_p),
                 ("n_t", C.c_int), ("seed", C.c_uint64), ("state_id", C.c_uint64), ("tag", C.c_int64),
                 ("F_out", C.c_void_p), ("stats", C.c_void_p), ("status_out", C.c_void_p),
-                ("basis_index", C.c_int64), ("kind", C.c_int)]
+                ("basis_index", C.c_int64), ("kind", C.c_int), ("otoc_out", C.c_void_p)]
 
 
 class PassInfo(C.Structure):
@@ -89,7 +89,11 @@ SIGNATURES = {
     "syk_batch_run": (_I, [_P, _I, _I, C.POINTER(_I), _P, _I]),
     "syk_batch_info": (_I, [_P, C.POINTER(_I), C.POINTER(_SZ), C.POINTER(_SZ)]),
     "syk_batch_job_bytes": (_SZ, [_P, _P, _I]),
+    "syk_otoc_exact_trace_batched": (_I, [_P, _I, _P, _D, _P, _I, _I, _SZ, C.POINTER(KrylovParams), _P, _P,
+                                          C.POINTER(KrylovStats)]),
     "syk_bounded_wait_selftest": (_I, [_P]),
+    "syk_probe_staging": (_I, [_P, _SZ, _I, _I, C.POINTER(_D), _P]),
+    "syk_probe_fp64": (_I, [C.POINTER(_D), _P]),
     "syk_last_error": (_I, [C.c_char_p, _SZ]),
     "syk_version": (C.c_char_p, []),
 }

@@ -51,6 +51,22 @@ def bounded_wait_selftest(stream=None) -> int:
     return int(L.load().syk_bounded_wait_selftest(_stream(stream)))
 
 
+def probe_staging(buf, reads: int, jobs_per_cta: int = 4096, stream=None) -> float:
+    """Bytes/s of the matvec's bulk-copy pipeline shape over the CUDA tensor
+    `buf` (syk_probe_staging; reads = -1, 0, 1 or 2)."""
+    v = C.c_double(0.0)
+    L.check(L.load().syk_probe_staging(_ptr(buf), buf.numel() * buf.element_size(), int(reads), int(jobs_per_cta),
+                                       C.byref(v), _stream(stream)))
+    return v.value
+
+
+def probe_fp64(stream=None) -> float:
+    """FP64 fused multiply-adds per second of the GPU (syk_probe_fp64)."""
+    v = C.c_double(0.0)
+    L.check(L.load().syk_probe_fp64(C.byref(v), _stream(stream)))
+    return v.value
+
+
 def compile_terms_host(N: int, quads, J, rep: str = "jw") -> dict:
     """Host-only term compilation (no GPU): x, z, coef_U, coef_D, imag arrays."""
     lib = L.load()
@@ -548,16 +564,17 @@ class Batch:
             raise ValueError("terms dtype differs from the batch dtype")
         tg = np.ascontiguousarray(np.asarray(t_grid, dtype=np.float64))
         F = np.zeros((len(tg), 2))
+        o = np.zeros(len(tg))
         st = L.KrylovStats()
         status = C.c_int(0)
         job = L.OtocJob(terms._h, int(a), int(b), float(beta), tg.ctypes.data, len(tg), C.c_uint64(seed),
                         C.c_uint64(state_id), int(tag), F.ctypes.data, C.addressof(st), C.addressof(status),
-                        int(basis_index), 1 if kind == "green" else 0)
+                        int(basis_index), 1 if kind == "green" else 0, o.ctypes.data)
         rc = self._lib.syk_batch_submit(self._h, C.byref(job))
         if rc == L.SYK_EAGAIN:
             return False
         L.check(rc)
-        self._pending[int(tag)] = (F, st, status, tg, terms)
+        self._pending[int(tag)] = (F, o, st, status, tg, terms)
         return True
 
     def run(self, max_ticks: int = 1 << 20, ticks_per_sync: int = 8):
@@ -567,9 +584,8 @@ class Batch:
         L.check(self._lib.syk_batch_run(self._h, int(max_ticks), int(ticks_per_sync), C.byref(n), tags, cap))
         out = []
         for i in range(min(n.value, cap)):
-            F, st, status, tg, _ = self._pending.pop(int(tags[i]))
-            Fc = F[:, 0] + 1j * F[:, 1]
-            out.append({"tag": int(tags[i]), "F": Fc, "otoc": Fc.real / Fc.real[0], "matvecs": st.matvecs,
+            F, o, st, status, tg, _ = self._pending.pop(int(tags[i]))
+            out.append({"tag": int(tags[i]), "F": F[:, 0] + 1j * F[:, 1], "otoc": o, "matvecs": st.matvecs,
                         "substeps": st.substeps, "status": status.value})
         return out
 
@@ -593,20 +609,16 @@ class Batch:
 def exact_trace_otoc(terms: "Terms", pairs, beta: float, t_grid, max_slots: int = 4096, max_bytes: int = 8 << 30,
                      m: int = 30, tol=None):
     """Exact-trace OTOC of Eq. (2) for each (a, b) in pairs, by the batched
-    engine over all 2D basis states: F_tr(t) = sum_g F_{e_g}(t) / 2D.
-    Returns {(a, b): (F complex [n_t], otoc [n_t])}."""
-    D = terms.D
-    tg = np.asarray(t_grid, dtype=np.float64)
-    acc = {tuple(p): np.zeros(len(tg), dtype=np.complex128) for p in pairs}
-    jobs = [(p, g) for p in acc for g in range(2 * D)]
-    with Batch(dtype=terms.dtype, max_slots=min(max_slots, len(jobs)), max_bytes=max_bytes, m=m, tol=tol) as b:
-        i = 0
-        while i < len(jobs) or b.pending:
-            while i < len(jobs):
-                (pa, pb), g = jobs[i]
-                if not b.submit(terms, pa, pb, beta, tg, 0, 0, i, basis_index=g):
-                    break
-                i += 1
-            for r in b.run(ticks_per_sync=16):
-                acc[jobs[r["tag"]][0]] += r["F"]
-    return {p: (F / (2 * D), (F / (2 * D)).real / (F / (2 * D)).real[0]) for p, F in acc.items()}
+    engine over all 2D basis states (syk_otoc_exact_trace_batched:
+    F_tr(t) = sum_g F_{e_g}(t) / 2D and OTOC = Re F_tr / Re F_tr(0), summed in
+    the library).  Returns {(a, b): (F complex [n_t], otoc [n_t])}."""
+    tg = np.ascontiguousarray(np.asarray(t_grid, dtype=np.float64))
+    pr = np.ascontiguousarray(np.asarray([tuple(p) for p in pairs], dtype=np.int32).reshape(-1, 2))
+    F = np.zeros((len(pr), len(tg), 2))
+    o = np.zeros((len(pr), len(tg)))
+    p = _params(m=m, tol=tol)
+    jobs = len(pr) * 2 * terms.D
+    L.check(terms._lib.syk_otoc_exact_trace_batched(terms._h, len(pr), pr.ctypes.data, float(beta), tg.ctypes.data,
+                                                    len(tg), int(min(max_slots, jobs)), int(max_bytes), C.byref(p),
+                                                    F.ctypes.data, o.ctypes.data, None))
+    return {(int(a), int(b)): (F[i, :, 0] + 1j * F[i, :, 1], o[i]) for i, (a, b) in enumerate(pr)}

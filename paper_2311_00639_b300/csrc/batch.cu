@@ -1061,6 +1061,8 @@ int syk_batch_run(syk_batch_t* h, int max_ticks, int ticks_per_sync, int* n_fini
       SYK_CUDA(cudaMemcpyAsync(jh.job.F_out, dev_slots[s].F, jh.job.n_t * 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                b.stream));
       SYK_CUDA(cudaStreamSynchronize(b.stream));
+      if (jh.job.otoc_out)  // normalised curve: Re F(t) / Re F(0)
+        for (int n = 0; n < jh.job.n_t; ++n) jh.job.otoc_out[n] = jh.job.F_out[2 * n] / jh.job.F_out[0];
       if (jh.job.stats) {
         jh.job.stats->matvecs = dev_slots[s].matvecs;
         jh.job.stats->substeps = dev_slots[s].substeps;

@@ -71,16 +71,13 @@ struct Params {
 };
 
 Params resolve(const syk_terms* h, const syk_krylov_params* p) {
+  const syk::KrylovSettings k = syk::krylov_settings(h->dtype, p);  // defaults and checks (entry.h)
   Params r;
-  r.m = (p && p->m) ? p->m : syk::default_krylov_m(h->dtype);
-  r.tol = (p && p->tol > 0) ? p->tol : (h->dtype == SYK_C128 ? 1e-12 : 1e-6);
-  r.max_sub = (p && p->max_substeps) ? p->max_substeps : 1000;
-  r.reorth = p && p->reorth;
-  r.two_pass = p && p->two_pass;
-  SYK_REQUIRE(r.m >= 1 && r.m <= syk::kMaxKrylov, "Krylov dimension m must be in [1, 64]");
-  SYK_REQUIRE(std::isfinite(r.tol) && r.tol > 0, "tol must be positive");
-  SYK_REQUIRE(r.max_sub >= 1, "max_substeps must be >= 1");
-  SYK_REQUIRE(!(r.reorth && r.two_pass), "reorth and two_pass cannot be combined");
+  r.m = k.m;
+  r.tol = k.tol;
+  r.max_sub = k.max_sub;
+  r.reorth = k.reorth;
+  r.two_pass = k.two_pass;
   return r;
 }
 

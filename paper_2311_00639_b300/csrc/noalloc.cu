@@ -10,16 +10,25 @@
 // the reduction partials and the device scalars come from the array below.
 //
 // Limits and sharing rules (also stated in include/syk.h):
-//   * the array holds kScratchBytes (16 MiB) on every GPU that loads the
-//     library, until the process exits;
+//   * the array holds kScratchBytes (16 MiB) on every GPU where the entry
+//     point has been called, until the process exits;
 //   * a call whose workspace (syk_krylov_workspace_bytes) is larger is
 //     rejected with SYK_EINVAL before any work is queued;
 //   * every call on a device uses the same array and leaves its contents
 //     behind; calls that overlap on the GPU (different streams, or host
 //     threads racing) corrupt each other, so serialise them;
 //   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (once per device, with that device current); make
-//     that first call before any stream capture.
+//     cudaGetSymbolAddress (once per device, with that device current).  CUDA
+//     loads this library's device code lazily, so that lookup is also when the
+//     16 MiB are reserved on the device: the first call does take device
+//     memory.  Callers that must not allocate later make one warm-up call at
+//     start-up, before any stream capture: a call with tau = t = 0 reserves
+//     the array (it only copies x to y); a real evolve also loads the kernels
+//     the later calls run.  Later calls allocate nothing;
+//   * the cached address belongs to the device context that was current at the
+//     first call; after cudaDeviceReset (or the primary context being released
+//     and created again) it is stale, like every handle of this library, so
+//     the library must not be used across a context reset.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,6 +36,7 @@
 #include <mutex>
 #include <string>
 
+#include "entry.h"
 #include "kernels.cuh"
 
 namespace {
@@ -71,13 +81,12 @@ extern "C" int syk_krylov_evolve_noalloc(const syk_terms_t* h, int block, double
     SYK_REQUIRE(x && y, "null x or y");
     SYK_REQUIRE(((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0,
                 "x and y must be 16-byte aligned");
-    const int m = (p && p->m) ? p->m : syk::default_krylov_m(h->dtype);
-    const double tol = (p && p->tol > 0) ? p->tol : (h->dtype == SYK_C128 ? 1e-12 : 1e-6);
-    const int max_sub = (p && p->max_substeps) ? p->max_substeps : 1000;
-    const bool reorth = p && p->reorth, two_pass = p && p->two_pass;
-    SYK_REQUIRE(m >= 1 && m <= syk::kMaxKrylov, "Krylov dimension m must be in [1, 64]");
-    SYK_REQUIRE(std::isfinite(tol) && tol > 0 && max_sub >= 1, "bad tol or max_substeps");
-    SYK_REQUIRE(!(reorth && two_pass), "reorth and two_pass cannot be combined");
+    // the same defaults and checks as syk_krylov_evolve
+    const syk::KrylovSettings ks = syk::krylov_settings(h->dtype, p);
+    const int m = ks.m;
+    const double tol = ks.tol;
+    const int max_sub = ks.max_sub;
+    const bool reorth = ks.reorth, two_pass = ks.two_pass;
     const size_t need = syk::krylov_ws_bytes(h, m, two_pass);
     if (need > kScratchBytes)
       throw syk::Error(SYK_EINVAL, "needs " + std::to_string(need) + " bytes of workspace; the static workspace of "
