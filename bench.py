@@ -44,10 +44,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="all",
-                    choices=["all", "otoc-batch", "otoc-serve", "n64-otoc", "spin", "nonherm"],
+                    choices=["all", "otoc-batch", "otoc-serve", "n64-otoc", "spin", "nonherm", "paper-rows", "config2"],
                     help="all: the benchmark line; otoc-batch / otoc-serve / n64-otoc / spin / nonherm: only that "
                          "leg, as its own JSON line (spin: random-field Heisenberg chain, H psi and OTOC curves; "
-                         "nonherm: non-Hermitian SYK, H psi and Arnoldi OTOC curves)")
+                         "nonherm: non-Hermitian SYK, H psi and Arnoldi OTOC curves; paper-rows: time per OTOC "
+                         "curve of the paper's benchmark rows; config2: the N=32 mixed-precision error statement)")
+    ap.add_argument("--rows-N", default="30,38,46", help="paper-rows: the N values (k=3, beta=0.05)")
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--k", type=float, default=4.0)
     ap.add_argument("--no-fp64", action="store_true")
@@ -340,7 +342,7 @@ def otoc_batched(args, syk, si, torch, rank=0):
            "realizations_per_s": R / wall, "curves_per_s": len(jobs) / wall, "wall_s": wall,
            "matvec_Gtermamp_s": termamps / wall / 1e9, "failed": sum(1 for v in results.values() if v["status"])}
     # plain FP64 single-realisation path (complex128, one realisation at a time)
-    nplain = min(2, R)
+    nplain = min(8, R)
     t0 = time.perf_counter()
     diffs = []
     for r in range(nplain):
@@ -388,6 +390,95 @@ def otoc_served(args, syk, torch):
                  "workload": f"{n} Poisson requests, N 28..48 (P ~ 0.7^((N-28)/2)), k 0.5..4, beta 2..20, "
                              f"t 0..{args.serve_tmax:g} step {args.serve_dt:g}, c64, HBM budget 100 GB"})
     return summ
+
+
+def paper_rows(args, syk, si, torch):
+    """The paper's benchmark rows (supplement Sec. I.B: time per OTOC curve,
+    one realisation, one state, t = 0..10 in 10 segments, sparse k = 3,
+    beta = 0.05) through the single-realisation path syk_otoc, complex128 and
+    complex64 (library Krylov defaults), one warm-up curve each."""
+    import numpy as np
+
+    grid = np.linspace(0.0, 10.0, 11)
+    rows = []
+    for N in [int(v) for v in args.rows_N.split(",")]:
+        q, J, _ = si.sample_sparse_syk(N, 3.0, r=0)
+        row = {"N": N, "k": 3, "beta": 0.05, "terms": len(J)}
+        for dtype in ("c128", "c64"):
+            with syk.Terms(N, q, J, dtype=dtype) as h:
+                h.otoc(N - 1, N - 2, 0.05, grid[:2], n_states=1, seed=9)  # warm-up (captures the Krylov loops)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                F, o, st = h.otoc(N - 1, N - 2, 0.05, grid, n_states=1, seed=9)
+                row[f"{dtype}_s_per_curve"] = time.perf_counter() - t0
+                row[f"{dtype}_matvecs"] = st.matvecs
+                row[f"{dtype}_substeps"] = st.substeps
+                row[f"{dtype}_otoc_t10"] = float(o[-1])
+        rows.append(row)
+    return {"workload": "paper benchmark rows, sparse k=3, beta=0.05, one Philox state, 11 t-points",
+            "rows": rows}
+
+
+def config2(args, syk, si, torch):
+    """The N=32 mixed-precision configuration: sparse SYK N=32, k=4
+    (realisation r=0), Lanczos m=30, 64 Philox typical states (seed 7, ids
+    0..63), t = 0..15 in steps of 0.1 (151 points), beta in {0, 5, 10}; every
+    curve in complex64 states (FP64 scalars) and in complex128, both through
+    the batched engine at the library's Krylov tolerances (1e-6 and 1e-12).  The complex64 error is stated against
+    the complex128 curves for all 64 x 3 curves, and both are compared with
+    the FP64 oracle's stored values (expm_multiply, states 0 and 1 at
+    t in {0, 0.1, 1, 2.5, 5, 10, 15}; tests/golden/otoc_N32_k4_r0_typical.txt)."""
+    import numpy as np
+
+    N, S = 32, 64
+    grid = np.round(np.arange(0.0, 15.0 + 1e-9, 0.1), 10)
+    betas = (0.0, 5.0, 10.0)
+    q, J, _ = si.sample_sparse_syk(N, 4.0, r=0)
+    gold_rows = np.loadtxt(os.path.join(ROOT, "tests", "golden", "otoc_N32_k4_r0_typical.txt"), comments="#")
+    curves, timing = {}, {}
+    for dtype, tol in (("c64", None), ("c128", None)):
+        with syk.Terms(N, q, J, dtype=dtype) as h, syk.Batch(dtype=dtype, max_slots=S * len(betas),
+                                                             max_bytes=16 << 30, m=30, tol=tol) as b:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tag = 0
+            keys = {}
+            for beta in betas:
+                for s in range(S):
+                    assert b.submit(h, N - 1, N - 2, beta, grid, 7, s, tag)
+                    keys[tag] = (beta, s)
+                    tag += 1
+            res = b.drain()
+            timing[dtype] = {"s": time.perf_counter() - t0, "curves": len(res),
+                             "matvecs": int(sum(r["matvecs"] for r in res)),
+                             "failed": sum(1 for r in res if r["status"])}
+            curves[dtype] = {keys[r["tag"]]: r["F"] for r in res}
+    out = {"workload": f"N={N}, k=4, T={len(J)}, m=30, {S} Philox states, 151 t-points (0..15, step 0.1), "
+                       "beta 0/5/10, batched engine", "timing": timing, "per_beta": {}}
+    worst = 0.0
+    for beta in betas:
+        errs = [float(np.max(np.abs(curves["c64"][(beta, s)] - curves["c128"][(beta, s)])) /
+                      np.max(np.abs(curves["c128"][(beta, s)]))) for s in range(S)]
+        m64 = np.mean([curves["c64"][(beta, s)] for s in range(S)], axis=0)
+        m128 = np.mean([curves["c128"][(beta, s)] for s in range(S)], axis=0)
+        o64, o128 = m64.real / m64.real[0], m128.real / m128.real[0]
+        r = gold_rows[gold_rows[:, 0] == beta]
+        vs_oracle = {}
+        for dtype in ("c64", "c128"):
+            e = 0.0
+            for s in (0, 1):
+                rs = r[r[:, 1] == s]
+                idx = [int(round(tv * 10)) for tv in rs[:, 2]]
+                Fg = rs[:, 3] + 1j * rs[:, 4]
+                e = max(e, float(np.max(np.abs(curves[dtype][(beta, s)][idx] - Fg)) / np.max(np.abs(Fg))))
+            vs_oracle[dtype] = e
+        out["per_beta"][f"{beta:g}"] = {"c64_vs_c128_max_rel_F": max(errs), "c64_vs_c128_median_rel_F": float(np.median(errs)),
+                                        "otoc_mean_max_abs_diff": float(np.max(np.abs(o64 - o128))),
+                                        "otoc_t15_c128": float(o128[-1]),
+                                        "vs_fp64_oracle_subset": vs_oracle}
+        worst = max(worst, max(errs), vs_oracle["c64"])
+    out["c64_vs_fp64_max_rel_F"] = worst
+    return out
 
 
 # ------------------------------------------------------------- spin chains --
@@ -872,6 +963,20 @@ def otoc_only(args):
                            "wall_s": wall, "matvecs": st.matvecs,
                            "substeps": st.substeps, "F": [[z.real, z.imag] for z in F[0]], "otoc": list(o),
                            "s_per_matvec": wall / max(1, st.matvecs)}}
+        print(json.dumps(line), flush=True)
+        return
+    if args.mode == "paper-rows":
+        res = paper_rows(args, syk, si, torch)
+        line = {"metric": "time per OTOC curve (the paper's benchmark rows: one realisation, one state, "
+                          "t = 0..10 in 10 segments)", "value": res["rows"][0]["c128_s_per_curve"], "unit": "s",
+                "higher_is_better": False, "config": res}
+        print(json.dumps(line), flush=True)
+        return
+    if args.mode == "config2":
+        res = config2(args, syk, si, torch)
+        line = {"metric": "complex64 OTOC error vs FP64 (N=32, 64 states, 151 points, beta 0/5/10)",
+                "value": res["c64_vs_fp64_max_rel_F"], "unit": "max |dF| / max |F|", "higher_is_better": False,
+                "config": res}
         print(json.dumps(line), flush=True)
         return
     if args.mode == "spin":

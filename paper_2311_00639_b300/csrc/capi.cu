@@ -135,6 +135,7 @@ void upload_table(syk_terms* h) {
       cudaFree(h->d_mem);
       h->d_mem = nullptr;
     }
+    h->clear_graphs();  // captured evolves point into the old table
     if (cudaMalloc(&h->d_mem, bytes) != cudaSuccess) {
       cudaGetLastError();
       throw syk::Error(SYK_ENOMEM, "device allocation of the term table failed");
@@ -385,6 +386,7 @@ int syk_krylov_evolve(const syk_terms_t* h, int block, double tau, double t, con
                 "workspace overlaps x or y");
     syk::KrylovResult tot;
     auto st = reinterpret_cast<cudaStream_t>(stream);
+    syk::krylov_totals_reset(workspace, st);
     for (int64_t s = 0; s < nstates; ++s) {
       const char* xs = static_cast<const char*>(x) + s * vb;
       char* ys = static_cast<char*>(y) + s * vb;
@@ -394,6 +396,7 @@ int syk_krylov_evolve(const syk_terms_t* h, int block, double tau, double t, con
       tot.substeps += r1.substeps;
       tot.err += r1.err;
     }
+    syk::krylov_totals_collect(workspace, st, tot);  // one synchronisation for the whole call
     if (stats) {
       stats->matvecs = tot.matvecs;
       stats->substeps = tot.substeps;

@@ -126,6 +126,20 @@ struct TermsView {
   const Real* coef;  // coefficients of the block being applied
 };
 
+// A captured single-realisation Krylov evolve: one substep as the body of a
+// CUDA-graph while-loop whose condition the tridiagonal step sets, for one
+// (block, output vector, workspace, m, reorth, two_pass).
+struct KrylovGraph {
+  int block = 0;
+  const void* y = nullptr;
+  const void* ws = nullptr;
+  int m = 0;
+  bool reorth = false, two_pass = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t used = 0;
+};
+
 }  // namespace syk
 
 struct syk_terms {
@@ -155,10 +169,25 @@ struct syk_terms {
   syk::PassPlan* d_pass_tail = nullptr;  // the last pass's tile order with no terms (epilogue after a split)
   int n_sm = 148;
   bool hermitian = true;  // false: complex couplings; Krylov propagation uses Arnoldi
+  // captured Krylov evolves (krylov.cu), least recently used dropped first;
+  // cleared whenever the device table is re-uploaded
+  mutable std::vector<syk::KrylovGraph> kgraphs;
+  mutable cudaStream_t cap_stream = nullptr;
+  mutable uint64_t kg_clock = 0;
+  void clear_graphs() const {
+    for (auto& g : kgraphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    kgraphs.clear();
+  }
   syk_terms() = default;
   syk_terms(const syk_terms&) = delete;
   syk_terms& operator=(const syk_terms&) = delete;
   ~syk_terms() {
+    if (!kgraphs.empty()) cudaDeviceSynchronize();
+    clear_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     if (d_mem) cudaFree(d_mem);
     if (d_split_ws) cudaFree(d_split_ws);
   }

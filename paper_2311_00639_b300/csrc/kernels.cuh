@@ -5,6 +5,15 @@
 
 namespace syk {
 
+// Counts summed on the device over the evolves that share one workspace (the
+// single-realisation Lanczos path keeps its substep control on the device).
+struct KTotals {
+  long long matvecs, substeps;
+  double err;  // sum of accepted local error estimates x accepted fractions
+  int fail;    // first failure: 1 no acceptable substep, 2 eigensolver, 3 max_substeps reached
+  int pad;
+};
+
 // Device-side scalars of one Lanczos run (float64 throughout).
 struct KScalars {
   double alpha[kMaxKrylov];
@@ -15,6 +24,13 @@ struct KScalars {
   double err;               // relative local error estimate of the accepted step
   int m_eff;                // basis vectors in use (< m after a breakdown)
   int status;               // 0 ok; 1 no acceptable substep; 2 eigensolver did not converge
+  // device-side substep control of one evolve (single-realisation path)
+  double z_re, z_im;  // the part of z = tau + i t still to be applied
+  double tol;
+  int n_sub, max_sub;
+  int fail;  // this evolve failed (see KTotals::fail)
+  int pad_;
+  KTotals tot;
 };
 
 inline size_t elem_bytes(int dtype) { return dtype == SYK_C128 ? 16 : 8; }
@@ -83,6 +99,13 @@ struct KrylovResult {
   int64_t matvecs = 0, substeps = 0;
   double err = 0.0;
 };
+// The Lanczos path of krylov_evolve_one queues its work and counts on the
+// device (KScalars::tot of the workspace): reset the totals before a sequence
+// of evolves that share a workspace, and collect them after it (collect
+// synchronises the stream, adds the counts to `acc` and throws SYK_ENOCONV if
+// an evolve failed).  The Arnoldi path still returns its counts directly.
+void krylov_totals_reset(void* ws, cudaStream_t st);
+void krylov_totals_collect(void* ws, cudaStream_t st, KrylovResult& acc);
 size_t krylov_ws_bytes(const syk_terms* h, int m, bool two_pass);
 // Arnoldi engine for a non-Hermitian H (arnoldi.cu); krylov_* dispatch to it
 // when h->hermitian is false.

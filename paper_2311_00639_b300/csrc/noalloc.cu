@@ -110,6 +110,7 @@ extern "C" int syk_krylov_evolve_noalloc(const syk_terms_t* h, int block, double
       tot.substeps += r.substeps;
       tot.err += r.err;
     }
+    syk::krylov_totals_collect(ws, st, tot);  // one synchronisation for the whole call
     if (stats) {
       stats->matvecs = tot.matvecs;
       stats->substeps = tot.substeps;

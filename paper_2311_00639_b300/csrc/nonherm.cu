@@ -79,6 +79,7 @@ void otoc_nh_run(const syk_terms* h, const syk_terms* hd, int a, int b, const do
   double* n2 = partial + 2 * G;
   double* Fdev = n2 + 8;
   SYK_CUDA(cudaMemsetAsync(Fdev, 0, static_cast<size_t>(rows) * n_t * 2 * sizeof(double), st));
+  krylov_totals_reset(ws.p, st);
   auto evolve = [&](const syk_terms* hh, int blk, double t, void* x) {
     KrylovResult r = krylov_evolve_one(hh, blk, 0.0, t, x, x, m, tol, max_sub, false, false, ws.p, st);
     tot.matvecs += r.matvecs;
@@ -129,6 +130,7 @@ void otoc_nh_run(const syk_terms* h, const syk_terms* hd, int a, int b, const do
   std::vector<double> Fh(static_cast<size_t>(rows) * n_t * 2);
   SYK_CUDA(cudaMemcpyAsync(Fh.data(), Fdev, Fh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   SYK_CUDA(cudaStreamSynchronize(st));
+  krylov_totals_collect(ws.p, st, tot);  // counts and failures of the queued Lanczos evolves
   if (F_raw) std::copy(Fh.begin(), Fh.end(), F_raw);
   if (otoc) {
     std::vector<double> mean(n_t, 0.0);

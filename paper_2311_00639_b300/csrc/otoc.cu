@@ -55,6 +55,7 @@ void otoc_run(const syk_terms* h, int a, int b, double beta, const double* tg, i
   double* n2 = partial + 2 * G;
   double* Fdev = n2 + 8;
   SYK_CUDA(cudaMemsetAsync(Fdev, 0, static_cast<size_t>(rows) * n_t * 2 * sizeof(double), st));
+  krylov_totals_reset(ws.p, st);
 
   auto evolve = [&](int blk, double tau, double t, void* x) {
     KrylovResult r = krylov_evolve_one(h, blk, tau, t, x, x, m, tol, max_sub, reorth, two_pass, ws.p, st);
@@ -108,6 +109,7 @@ void otoc_run(const syk_terms* h, int a, int b, double beta, const double* tg, i
   std::vector<double> Fh(static_cast<size_t>(rows) * n_t * 2);
   SYK_CUDA(cudaMemcpyAsync(Fh.data(), Fdev, Fh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   SYK_CUDA(cudaStreamSynchronize(st));
+  krylov_totals_collect(ws.p, st, tot);  // counts and failures of the queued Lanczos evolves
   if (F_raw) std::copy(Fh.begin(), Fh.end(), F_raw);
   if (otoc) {
     std::vector<double> mean(n_t, 0.0);

@@ -175,6 +175,7 @@ void pauli_otoc_run(const syk_terms* h, uint32_t wx, uint32_t wz, uint32_t vx, u
   double* n2 = partial + 2 * G;
   double* Fdev = n2 + 8;
   SYK_CUDA(cudaMemsetAsync(Fdev, 0, static_cast<size_t>(rows) * n_t * 2 * sizeof(double), st));
+  krylov_totals_reset(ws.p, st);
 
   auto evolve = [&](double tau, double t, void* x) {
     KrylovResult r = krylov_evolve_one(h, 0, tau, t, x, x, m, tol, max_sub, reorth, two_pass, ws.p, st);
@@ -219,6 +220,7 @@ void pauli_otoc_run(const syk_terms* h, uint32_t wx, uint32_t wz, uint32_t vx, u
   std::vector<double> Fh(static_cast<size_t>(rows) * n_t * 2);
   SYK_CUDA(cudaMemcpyAsync(Fh.data(), Fdev, Fh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   SYK_CUDA(cudaStreamSynchronize(st));
+  krylov_totals_collect(ws.p, st, tot);  // counts and failures of the queued Lanczos evolves
   if (F_raw) std::copy(Fh.begin(), Fh.end(), F_raw);
   if (otoc) {
     std::vector<double> mean(n_t, 0.0);

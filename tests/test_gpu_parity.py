@@ -455,3 +455,34 @@ def test_krylov_tiny_blocks(syk, dtype, N):
             for z in (2.0j, 0.5 - 1.0j):
                 y, _ = h.krylov_evolve(to_dev(x, dtype), blk, z.real, z.imag)
                 assert rel_err(y.cpu().numpy(), dyn.evolve(Hb, z, x)) < lim, (dtype, N, blk, z)
+
+
+def test_krylov_device_substep_control(syk):
+    """The substep loop runs on the device (a captured while-loop whose
+    condition the tridiagonal step sets): a long evolve takes several substeps
+    with m matvecs each; the same call again (the cached loop) and into
+    another output buffer (a new loop) give the same vector; max_substeps
+    below what the step needs fails with SYK_ENOCONV, and the handle still
+    evolves correctly afterwards."""
+    from paper_2311_00639_b300 import _lib as L
+
+    t = torch()
+    N = 16
+    q, J, _ = si.sample_sparse_syk(N, 4, r=4)
+    HU, _ = ham.blocks(ham.dense_H(N, q, J, "jw"), N, "jw")
+    x = rand_vec(HU.shape[0], 9)
+    ref = dyn.evolve(HU, complex(0.3, 40.0), x)
+    with syk.Terms(N, q, J, dtype="c128") as h:
+        xd = to_dev(x, "c128")
+        y1, st = h.krylov_evolve(xd, 0, 0.3, 40.0, m=12, tol=1e-13)
+        assert st.substeps > 1 and st.matvecs == 12 * st.substeps
+        assert rel_err(y1.cpu().numpy(), ref) < 1e-10
+        y2, st2 = h.krylov_evolve(xd, 0, 0.3, 40.0, m=12, tol=1e-13, y=y1)
+        assert st2.substeps == st.substeps and t.equal(y1, y2)
+        y3, _ = h.krylov_evolve(xd, 0, 0.3, 40.0, m=12, tol=1e-13)
+        assert t.equal(y1, y3)
+        with pytest.raises(L.SykError) as ei:
+            h.krylov_evolve(xd, 0, 0.3, 40.0, m=12, tol=1e-13, max_substeps=1)
+        assert ei.value.code == L.SYK_ENOCONV
+        y4, _ = h.krylov_evolve(xd, 0, 0.3, 40.0, m=12, tol=1e-13)
+        assert t.equal(y1, y4)
