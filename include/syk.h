@@ -543,6 +543,21 @@ int syk_otoc_exact_trace_batched(const syk_terms_t* h, int n_pairs, const int32_
 int syk_bounded_wait_selftest(syk_stream_t stream);
 
 /*
+ * syk_tridiag_exp — the projected-exponential step of the Krylov engine on a
+ * caller's Lanczos matrix (supplement Sec. I.A, the Krylov time evolution;
+ * exposed for testing): T = tridiag(beta[0..m-2], alpha[0..m-1],
+ * beta[0..m-2]) with residual beta[m-1] (HOST arrays of m; beta >= 0), the
+ * largest fraction s = 2^-k of z = z_re + i z_im whose a-posteriori error
+ * estimate is <= tol * s, and c = e^{-s z T} e_1.  force_ql = 1 takes the QL
+ * eigensolver instead of the lane-parallel one.  Outputs (HOST): c [m][2]
+ * (re, im), *s_acc (0 if no fraction passed), *err, *used_ql (1 if the QL
+ * path ran; may be NULL).  Blocking, on the legacy default stream.  Errors:
+ * SYK_EINVAL, SYK_ENOMEM, SYK_ENOCONV, SYK_ECUDA.
+ */
+int syk_tridiag_exp(int m, const double* alpha, const double* beta, double z_re, double z_im, double tol, int force_ql,
+                    double* c, double* s_acc, double* err, int* used_ql);
+
+/*
  * Hardware probes for the benchmark's roofline denominators (no paper
  * counterpart; the hot path never calls them).  Both synchronise `stream`.
  *

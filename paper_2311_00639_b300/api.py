@@ -60,6 +60,21 @@ def probe_staging(buf, reads: int, jobs_per_cta: int = 4096, stream=None) -> flo
     return v.value
 
 
+def tridiag_exp(alpha, beta, z: complex, tol: float, force_ql: bool = False):
+    """The Krylov engine's projected-exponential step on a given Lanczos matrix
+    (syk_tridiag_exp): returns (c complex [m], s_acc, err, used_ql)."""
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(beta, dtype=np.float64))
+    if a.shape != b.shape:
+        raise ValueError("alpha and beta lengths differ")
+    c = np.zeros((len(a), 2))
+    s, e, q = C.c_double(0.0), C.c_double(0.0), C.c_int(0)
+    L.check(L.load().syk_tridiag_exp(len(a), a.ctypes.data, b.ctypes.data, float(np.real(z)), float(np.imag(z)),
+                                     float(tol), int(bool(force_ql)), c.ctypes.data, C.byref(s), C.byref(e),
+                                     C.byref(q)))
+    return c[:, 0] + 1j * c[:, 1], s.value, e.value, bool(q.value)
+
+
 def probe_fp64(stream=None) -> float:
     """FP64 fused multiply-adds per second of the GPU (syk_probe_fp64)."""
     v = C.c_double(0.0)

@@ -11,7 +11,7 @@ struct KTotals {
   long long matvecs, substeps;
   double err;  // sum of accepted local error estimates x accepted fractions
   int fail;    // first failure: 1 no acceptable substep, 2 eigensolver, 3 max_substeps reached
-  int pad;
+  int ql;      // substeps whose eigensystem came from the QL fallback (tridiag.cuh)
 };
 
 // Device-side scalars of one Lanczos run (float64 throughout).

@@ -33,6 +33,12 @@ __global__ void __launch_bounds__(32) k_tridiag(KScalars* sc, int m, double z_re
   tridiag_warp(sc, m, z_re, z_im, tol, Z);
 }
 
+__global__ void __launch_bounds__(32) k_tridiag_test(KScalars* sc, int m, double z_re, double z_im, double tol,
+                                                    int allow_lane_parallel) {
+  __shared__ double Z[kMaxKrylov][kMaxKrylov + 1];
+  tridiag_warp(sc, m, z_re, z_im, tol, Z, allow_lane_parallel != 0);
+}
+
 // Start of one evolve: the remaining step is all of z, no substep taken yet.
 __global__ void k_evolve_init(KScalars* sc, double tau, double t, double tol, int max_sub) {
   sc->z_re = tau;
@@ -272,3 +278,43 @@ KrylovResult krylov_evolve_one(const syk_terms* h, int block, double tau, double
 }
 
 }  // namespace syk
+
+extern "C" int syk_tridiag_exp(int m, const double* alpha, const double* beta, double z_re, double z_im, double tol,
+                               int force_ql, double* c, double* s_acc, double* err, int* used_ql) {
+  syk::KScalars* d = nullptr;
+  int rc = SYK_OK;
+  try {
+    SYK_REQUIRE(m >= 1 && m <= syk::kMaxKrylov, "m must be in [1, 64]");
+    SYK_REQUIRE(alpha && beta && c && s_acc && err, "null argument");
+    SYK_REQUIRE(std::isfinite(z_re) && std::isfinite(z_im) && std::isfinite(tol) && tol > 0, "bad z or tol");
+    syk::KScalars h{};
+    for (int i = 0; i < m; ++i) {
+      SYK_REQUIRE(std::isfinite(alpha[i]) && std::isfinite(beta[i]) && beta[i] >= 0.0, "bad alpha or beta");
+      h.alpha[i] = alpha[i];
+      h.beta[i] = beta[i];
+    }
+    h.m_eff = m;
+    if (cudaMalloc(&d, sizeof(syk::KScalars)) != cudaSuccess) {
+      cudaGetLastError();
+      d = nullptr;
+      throw syk::Error(SYK_ENOMEM, "device allocation failed");
+    }
+    SYK_CUDA(cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice));
+    syk::k_tridiag_test<<<1, 32>>>(d, m, z_re, z_im, tol, force_ql ? 0 : 1);
+    SYK_CUDA(cudaGetLastError());
+    SYK_CUDA(cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < m; ++i) {
+      c[2 * i] = h.c_re[i];
+      c[2 * i + 1] = h.c_im[i];
+    }
+    *s_acc = h.s_acc;
+    *err = h.err;
+    if (used_ql) *used_ql = h.tot.ql;
+    if (h.status == 2) throw syk::Error(SYK_ENOCONV, "tridiagonal eigensolver did not converge");
+  } catch (const syk::Error& e) {
+    syk::set_last_error(std::string("syk_tridiag_exp: ") + e.what());
+    rc = e.code;
+  }
+  if (d) cudaFree(d);
+  return rc;
+}

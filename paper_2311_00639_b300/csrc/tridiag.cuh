@@ -1,6 +1,31 @@
-// Projected exponential of a Lanczos run (FP64, one warp): implicit QL on the
-// symmetric tridiagonal T, then the substep search.  Shared by the
+// Projected exponential of a Lanczos run (FP64, one warp): the eigensystem of
+// the symmetric tridiagonal T, then the substep search.  Shared by the
 // single-state and batched engines.
+//
+// Eigensystem.  FP64 instructions are scarce on this part (a warp-wide DFMA
+// costs about as much as 64 cycles of issue, whatever the active lanes), so
+// the default path gives every lane its own eigenvalue and eigenvector and
+// keeps each lane's work to a few O(n) recurrences:
+//   1. bisection on the Sturm count (LDL^T pivots, Wilkinson's sign rule) in
+//      FP32 locates eigenvalue k of T for lane k;
+//   2. Newton's method on the characteristic polynomial det(T_i - x), its
+//      three-term recurrence and derivative in FP64, polishes it, safeguarded
+//      by the Sturm count of the same recurrence (sign changes along the
+//      leading minors: the bracket always holds eigenvalue k);
+//   3. the eigenvector from the two three-term recurrences (from the top row
+//      and from the bottom row), joined at the row where the product of the
+//      two solutions is largest: that row maximises |[(T - x)^{-1}]_rr|, the
+//      twisted-factorisation choice (Dhillon and Parlett's MRRR) that keeps
+//      both halves accurate.
+// The result is accepted when every lane's Newton iteration converged, the
+// eigenvalues come out strictly increasing, and the eigensystem reproduces
+// the first columns of T^0 and T^1 to 1e-13 (the step only needs
+// c = sum_k f(lam_k) z_k z_k[0], and vectors of nearly equal eigenvalues,
+// which come out mixed, err in c as in these sums); otherwise (tight
+// clusters, e.g. converged Ritz values of a small block) the warp
+// falls back to the implicit QL algorithm with Wilkinson shifts (the tql2
+// procedure of Bowdler, Martin, Reinsch and Wilkinson, Handbook for Automatic
+// Computation II), every lane running the same recurrence.
 #pragma once
 
 #include <cfloat>
@@ -46,26 +71,251 @@ __device__ inline double warp_sum_(double v) {
   return v;
 }
 
-// One warp.  Every lane runs the same scalar QL recurrence on its own copy
-// of (d, e) and rotates the eigenvector rows k = lane, lane + 32 it owns.
-// Z is shared scratch of kMaxKrylov x (kMaxKrylov + 1) doubles.
-__device__ void tridiag_warp(KScalars* sc, int m, double z_re, double z_im, double tol,
-                             double (*Z)[kMaxKrylov + 1]) {
-  const int lane = threadIdx.x & 31;
-  const int n = min(sc->m_eff, m);
-  if (n <= 0) {  // x = 0
-    if (lane == 0) {
-      sc->s_acc = 1.0;
-      sc->err = 0.0;
-    }
-    return;
+// Sturm count below x in FP32: the number of negative pivots of the LDL^T
+// factorisation of T - x (a zero pivot is replaced by -pivmin).
+__device__ inline int sturm_count_f32(int n, const float* df, const float* e2f, float x, float pivmin) {
+  float q = df[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int c = q < 0.f ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    q = (df[i] - x) - __fdiv_rn(e2f[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f ? 1 : 0;
   }
+  return c;
+}
+
+// det(T_i - x) for the leading i x i blocks by the three-term recurrence, in
+// FP64: returns p_n, dp_n/dx and the number of sign changes along
+// p_0 .. p_n (= eigenvalues below x).  Pairs of consecutive values are
+// rescaled by 2^-/+600 when they leave [2^-600, 2^600] (the ratio p/dp is
+// unchanged).
+struct CharPoly {
+  double p, dp;
+  int below;
+};
+__device__ inline CharPoly char_poly(int n, const double* d, const double* e2, double x) {
+  double p0 = 1.0, dp0 = 0.0;
+  double p1 = d[0] - x, dp1 = -1.0;
+  if (p1 == 0.0) p1 = -0x1p-900;
+  int below = p1 < 0.0 ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    const double a = d[i] - x;
+    double p2 = fma(a, p1, -e2[i - 1] * p0);
+    const double dp2 = fma(a, dp1, -fma(e2[i - 1], dp0, p1));
+    if (p2 == 0.0) p2 = (p1 < 0.0 ? 0x1p-900 : -0x1p-900) * fabs(p1);
+    below += ((p2 < 0.0) != (p1 < 0.0)) ? 1 : 0;
+    p0 = p1;
+    dp0 = dp1;
+    p1 = p2;
+    dp1 = dp2;
+    const int ex = (__double2hiint(p1) >> 20) & 0x7FF;
+    if (ex > 1023 + 600) {
+      p0 *= 0x1p-600;
+      p1 *= 0x1p-600;
+      dp0 *= 0x1p-600;
+      dp1 *= 0x1p-600;
+    } else if (ex < 1023 - 600 && ((__double2hiint(p0) >> 20) & 0x7FF) < 1023 - 600) {
+      p0 *= 0x1p600;
+      p1 *= 0x1p600;
+      dp0 *= 0x1p600;
+      dp1 *= 0x1p600;
+    }
+  }
+  return {p1, dp1, below};
+}
+
+// Unbiased binary exponent of |v| (v != 0), from its bits.
+__device__ inline int exp2_of(double v) { return ((__double2hiint(v) >> 20) & 0x7FF) - 1023; }
+
+// Lane-parallel eigensystem of T (see the header): eigenvalue k of lane k
+// (and k + 32) in lam[0] (lam[1]), eigenvector k in column k of Z.  Returns
+// false when the checks fail (the caller then runs the QL path).
+__device__ bool eig_lane_parallel(const KScalars* sc, int n, double (*Z)[kMaxKrylov + 1], double (&lam)[2]) {
+  __shared__ double sd[kMaxKrylov], se[kMaxKrylov], se2[kMaxKrylov], sinv[kMaxKrylov];
+  __shared__ float sdf[kMaxKrylov], se2f[kMaxKrylov];
+  const int lane = threadIdx.x & 31;
+  double glo = 1e300, ghi = -1e300, emax2 = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double di = sc->alpha[i];
+    const double ei = i < n - 1 ? sc->beta[i] : 0.0;
+    const double ep = i > 0 ? sc->beta[i - 1] : 0.0;
+    sd[i] = di;
+    se[i] = ei;
+    se2[i] = ei * ei;
+    sinv[i] = i < n - 1 ? 1.0 / ei : 0.0;
+    sdf[i] = static_cast<float>(di);
+    se2f[i] = static_cast<float>(ei * ei);
+    glo = fmin(glo, di - fabs(ei) - fabs(ep));  // Gershgorin
+    ghi = fmax(ghi, di + fabs(ei) + fabs(ep));
+    emax2 = fmax(emax2, ei * ei);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+    emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
+  }
+  __syncwarp();
+  const double tnorm = fmax(fabs(glo), fabs(ghi));
+  const double width = ghi - glo;
+  if (!(width > 0.0) || !(tnorm < 1e300)) return false;
+  const float pivmin = static_cast<float>(fmax(1.0, emax2) * 1e-30);
+  const double eps = 0x1p-52;
+  bool ok = true;
+  for (int slot = 0; slot < 2; ++slot) {
+    const int k = lane + 32 * slot;
+    if (slot == 1 && n <= 32) break;
+    double xk = 0.0;
+    if (k < n) {
+      // 1. FP32 bisection for the k-th eigenvalue (0-based, ascending)
+      float a = static_cast<float>(glo - 1e-6 * width), b = static_cast<float>(ghi + 1e-6 * width);
+      for (int it = 0; it < 30; ++it) {
+        const float mid = 0.5f * (a + b);
+        if (!(mid > a && mid < b)) break;
+        if (sturm_count_f32(n, sdf, se2f, mid, pivmin) > k)
+          b = mid;
+        else
+          a = mid;
+      }
+      // 2. FP64 Newton on det(T - x), bracketed by the Sturm count
+      double A = static_cast<double>(a) - 4.0 * (static_cast<double>(b) - a) - 1e-6 * width;
+      double B = static_cast<double>(b) + 4.0 * (static_cast<double>(b) - a) + 1e-6 * width;
+      double x = 0.5 * (static_cast<double>(a) + static_cast<double>(b));
+      bool conv = false;
+      for (int it = 0; it < 12 && !conv; ++it) {
+        const CharPoly cp = char_poly(n, sd, se2, x);
+        if (cp.below > k)
+          B = x;
+        else
+          A = x;
+        // a Newton step at rounding level ends the iteration (the iterate may
+        // then sit on the bracket's end, where the count put it)
+        const double step = (cp.dp != 0.0) ? cp.p / cp.dp : 1e300;
+        if (fabs(step) <= 4.0 * eps * fmax(fabs(x), 1e-3 * tnorm)) {
+          conv = true;
+          x -= step;
+          break;
+        }
+        double xn = x - step;
+        if (!(xn > A && xn < B)) xn = 0.5 * (A + B);
+        x = xn;
+      }
+      ok = ok && conv;
+      xk = x;
+      // 3. eigenvector: x_i from the top (x_0 = 1), y_i from the bottom
+      //    (y_{n-1} = 1), stored with a power-of-two scale count each
+      double xv[kMaxKrylov], yv[kMaxKrylov];
+      int xs[kMaxKrylov], ys[kMaxKrylov];
+      {
+        double u0 = 0.0, u1 = 1.0;
+        int sc_ = 0;
+        xv[0] = 1.0;
+        xs[0] = 0;
+        for (int i = 0; i + 1 < n; ++i) {
+          double u2 = fma(x - sd[i], u1, -(i > 0 ? se[i - 1] : 0.0) * u0) * sinv[i];
+          if (exp2_of(u2) > 600 && u2 != 0.0) {
+            u2 *= 0x1p-600;
+            u1 *= 0x1p-600;
+            ++sc_;
+          }
+          xv[i + 1] = u2;
+          xs[i + 1] = sc_;
+          u0 = u1;
+          u1 = u2;
+        }
+      }
+      {
+        double u0 = 0.0, u1 = 1.0;
+        int sc_ = 0;
+        yv[n - 1] = 1.0;
+        ys[n - 1] = 0;
+        for (int i = n - 1; i > 0; --i) {
+          double u2 = fma(x - sd[i], u1, -(i < n - 1 ? se[i] : 0.0) * u0) * sinv[i - 1];
+          if (exp2_of(u2) > 600 && u2 != 0.0) {
+            u2 *= 0x1p-600;
+            u1 *= 0x1p-600;
+            ++sc_;
+          }
+          yv[i - 1] = u2;
+          ys[i - 1] = sc_;
+          u0 = u1;
+          u1 = u2;
+        }
+      }
+      // join at the row r maximising |x_r y_r| (scale counts included)
+      int r = 0;
+      int best = -0x7FFFFFFF;
+      for (int i = 0; i < n; ++i) {
+        const double pr = xv[i] * yv[i];
+        const int e = (pr != 0.0 ? exp2_of(pr) : -5000) + 600 * (xs[i] + ys[i]);
+        if (e > best) {
+          best = e;
+          r = i;
+        }
+      }
+      const double ixr = 1.0 / xv[r], iyr = 1.0 / yv[r];
+      double nrm = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const int ds = (i <= r) ? xs[i] - xs[r] : ys[i] - ys[r];  // <= 0
+        double v = (i <= r) ? xv[i] * ixr : yv[i] * iyr;
+        if (ds != 0) v = ds < -1 ? 0.0 : v * 0x1p-600;
+        xv[i] = v;
+        nrm = fma(v, v, nrm);
+      }
+      const double inv = rsqrt(nrm);
+      for (int i = 0; i < n; ++i) Z[i][k] = xv[i] * inv;
+    }
+    lam[slot] = xk;
+  }
+  __syncwarp();
+  // checks: eigenvalues strictly increasing (relative gaps >= 1e-7), and the
+  // eigensystem reproduces the first column of T^0 and T^1:
+  // sum_k z_k z_k[0] = e_1 and sum_k lam_k z_k z_k[0] = T e_1 to 1e-13.  The
+  // step uses c = sum_k f(lam_k) z_k z_k[0]; errors of nearly equal lam_k
+  // (whose vectors mix) enter c as these two sums do, so passing them bounds
+  // the eigenvector part of the error of c.
+  __shared__ double slam[kMaxKrylov];
+  for (int slot = 0; slot < 2; ++slot) {
+    const int k = lane + 32 * slot;
+    if (k < n) slam[k] = lam[slot];
+  }
+  __syncwarp();
+  const double next0 = __shfl_down_sync(0xffffffffu, lam[0], 1);
+  const double next1 = __shfl_down_sync(0xffffffffu, lam[1], 1);
+  const double first1 = __shfl_sync(0xffffffffu, lam[1], 0);
+  for (int slot = 0; slot < 2; ++slot) {
+    const int i = lane + 32 * slot;
+    if (i + 1 < n) {
+      const double nx = (slot == 0) ? (lane < 31 ? next0 : first1) : next1;
+      if (!(nx - lam[slot] >= 1e-7 * width)) ok = false;
+    }
+    if (i < n) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double w = Z[i][k] * Z[0][k];
+        s0 += w;
+        s1 = fma(w, slam[k], s1);
+      }
+      const double t0 = i == 0 ? 1.0 : 0.0;
+      const double t1 = i == 0 ? sd[0] : (i == 1 ? se[0] : 0.0);
+      if (!(fabs(s0 - t0) <= 1e-13) || !(fabs(s1 - t1) <= 1e-13 * tnorm)) ok = false;
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Implicit QL with Wilkinson shifts (tql2, see the header): every lane runs
+// the same recurrence on its own copy of (d, e) and rotates the eigenvector
+// rows k = lane, lane + 32 it owns.  Returns 0, or 2 if an eigenvalue needed
+// more than 100 iterations.
+__device__ int tridiag_ql(const KScalars* sc, int n, double (*Z)[kMaxKrylov + 1], double (&lam)[2]) {
+  const int lane = threadIdx.x & 31;
   double d[kMaxKrylov], e[kMaxKrylov];
   for (int i = 0; i < n; ++i) {
     d[i] = sc->alpha[i];
     e[i] = (i < n - 1) ? sc->beta[i] : 0.0;
   }
-  const double resid = sc->beta[n - 1];
   for (int k = lane; k < n; k += 32)
     for (int i = 0; i < n; ++i) Z[k][i] = (i == k) ? 1.0 : 0.0;
   __syncwarp();
@@ -123,20 +373,30 @@ __device__ void tridiag_warp(KScalars* sc, int m, double z_re, double z_im, doub
     if (status) break;
   }
   __syncwarp();
-  // Substep search: largest s = 2^-k with estimated local error <= tol * s.
-  // Estimates (relative to ||c||): beta_m |e_m^T e^{-hT} e_1| and
-  // beta_m |h| |e_m^T phi_1(-hT) e_1| (Saad 1992, Thm. 5.1), the larger one.
-  // Each lane evaluates the exponentials of its own eigenvalues (k = lane,
-  // lane + 32) once per attempt; the small products then use shared memory.
+  lam[0] = lane < n ? d[lane] : 0.0;
+  lam[1] = lane + 32 < n ? d[lane + 32] : 0.0;
+  return status;
+}
+
+// Substep search on the eigensystem (lam, Z) of T: largest s = 2^-k with
+// estimated local error <= tol * s.  Estimates (relative to ||c||):
+// beta_m |e_m^T e^{-hT} e_1| and beta_m |h| |e_m^T phi_1(-hT) e_1| (Saad 1992,
+// Thm. 5.1), the larger one.  Each lane evaluates the exponentials of its own
+// eigenvalues (k = lane, lane + 32) once per attempt; the small products then
+// use shared memory.
+__device__ void substep_search(KScalars* sc, int n, int m, double resid, double z_re, double z_im, double tol,
+                               double (*Z)[kMaxKrylov + 1], const double (&lam)[2], int status) {
+  const int lane = threadIdx.x & 31;
   __shared__ double Er[kMaxKrylov], Ei[kMaxKrylov], Pr[kMaxKrylov], Pi[kMaxKrylov];
   double s_frac = 1.0, err = 0.0;
   bool ok = false;
   for (int attempt = 0; attempt < 64 && status == 0; ++attempt) {
     const double hr = s_frac * z_re, hi = s_frac * z_im;
-    for (int k = lane; k < n; k += 32) {
+    for (int k = lane, slot = 0; k < n; k += 32, ++slot) {
       const double w0 = Z[0][k];
-      const double2 ex = cexp_(-hr * d[k], -hi * d[k]);
-      const double2 ph = phi1_(-hr * d[k], -hi * d[k]);
+      const double dk = lam[slot];
+      const double2 ex = cexp_(-hr * dk, -hi * dk);
+      const double2 ph = phi1_(-hr * dk, -hi * dk);
       Er[k] = ex.x * w0;
       Ei[k] = ex.y * w0;
       Pr[k] = ph.x * w0;
@@ -188,6 +448,32 @@ __device__ void tridiag_warp(KScalars* sc, int m, double z_re, double z_im, doub
     sc->err = err;
     sc->status = status ? status : (ok ? 0 : 1);
   }
+}
+
+// One warp.  Eigensystem by the lane-parallel path, or by implicit QL where
+// every lane runs the same scalar recurrence on its own copy of (d, e) and
+// rotates the eigenvector rows k = lane, lane + 32 it owns.  Z is shared
+// scratch of kMaxKrylov x (kMaxKrylov + 1) doubles.
+__device__ void tridiag_warp(KScalars* sc, int m, double z_re, double z_im, double tol,
+                             double (*Z)[kMaxKrylov + 1], bool allow_lane_parallel = true) {
+  const int lane = threadIdx.x & 31;
+  const int n = min(sc->m_eff, m);
+  if (n <= 0) {  // x = 0
+    if (lane == 0) {
+      sc->s_acc = 1.0;
+      sc->err = 0.0;
+    }
+    return;
+  }
+  double lam[2] = {0.0, 0.0};
+  int status = 0;
+  const double resid = sc->beta[n - 1];
+  if (n == 1 || !allow_lane_parallel || !eig_lane_parallel(sc, n, Z, lam)) {
+    status = tridiag_ql(sc, n, Z, lam);
+    if ((threadIdx.x & 31) == 0) sc->tot.ql += 1;
+  }
+  __syncwarp();
+  substep_search(sc, n, m, resid, z_re, z_im, tol, Z, lam, status);
 }
 
 }  // namespace
