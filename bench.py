@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--spin-otoc-L", type=int, default=20, help="spin leg: qubits of the OTOC-curve chain")
     ap.add_argument("--spin-beta", type=float, default=0.0,
                     help="spin leg: inverse temperature of the OTOC curves (0: infinite temperature)")
+    ap.add_argument("--serve-hbm-gb", type=float, default=150.0, help="served leg: device arena for live jobs")
+    ap.add_argument("--serve-slots", type=int, default=256, help="served leg: jobs live at once")
+    ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "sjf"],
+                    help="served leg: admission order (fifo, or shortest estimated work first)")
     ap.add_argument("--serve-load", type=float, default=0.75,
                     help="Poisson arrival rate as a fraction of the closed-loop capacity (all requests at t=0)")
     return ap.parse_args()
@@ -368,19 +372,27 @@ def otoc_served(args, syk, torch):
     weighted toward small N, k in {0.5,1,2,4}, beta in {2,5,10,20}; the arrival
     rate is set to ~75% of the capacity measured by a closed-loop pass."""
     from paper_2311_00639_b300 import serve
+    import syk_inputs as si
 
     kw = dict(t_max=args.serve_tmax, dt=args.serve_dt)
     n = args.serve_requests
+    hbm = int(args.serve_hbm_gb * (1 << 30))
+
+    def workload(rate, seed):
+        return [serve.Request(**r) for r in si.served_requests(n, rate=rate, seed=seed, **kw)]
+
     # capacity: all requests present at t=0
-    cap_reqs = serve.served_workload(n, rate=1e9, seed=11, **kw)
-    srv = serve.OtocServer(dtype="c64", max_slots=256, hbm_budget_bytes=100 << 30, ticks_per_step=8)
+    cap_reqs = workload(1e9, 11)
+    srv = serve.OtocServer(dtype="c64", max_slots=args.serve_slots, hbm_budget_bytes=hbm, ticks_per_step=8,
+                           policy=args.serve_policy)
     t0 = time.perf_counter()
     res = srv.run(cap_reqs)
     cap = len(res) / (time.perf_counter() - t0)
     srv.close()
     rate = args.serve_load * cap
-    reqs = serve.served_workload(n, rate=rate, seed=12, **kw)
-    srv = serve.OtocServer(dtype="c64", max_slots=256, hbm_budget_bytes=100 << 30, ticks_per_step=8)
+    reqs = workload(rate, 12)
+    srv = serve.OtocServer(dtype="c64", max_slots=args.serve_slots, hbm_budget_bytes=hbm, ticks_per_step=8,
+                           policy=args.serve_policy)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
@@ -388,7 +400,8 @@ def otoc_served(args, syk, torch):
     summ = serve.summarize(res, wall)
     summ.update({"arrival_rate_per_s": rate, "closed_loop_capacity_per_s": cap, "load": args.serve_load,
                  "workload": f"{n} Poisson requests, N 28..48 (P ~ 0.7^((N-28)/2)), k 0.5..4, beta 2..20, "
-                             f"t 0..{args.serve_tmax:g} step {args.serve_dt:g}, c64, HBM budget 100 GB"})
+                             f"t 0..{args.serve_tmax:g} step {args.serve_dt:g}, c64, HBM budget "
+                             f"{args.serve_hbm_gb:g} GiB, {args.serve_slots} slots, admission {args.serve_policy}"})
     return summ
 
 

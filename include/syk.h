@@ -551,11 +551,12 @@ int syk_bounded_wait_selftest(syk_stream_t stream);
  * estimate is <= tol * s, and c = e^{-s z T} e_1.  force_ql = 1 takes the QL
  * eigensolver instead of the lane-parallel one.  Outputs (HOST): c [m][2]
  * (re, im), *s_acc (0 if no fraction passed), *err, *used_ql (1 if the QL
- * path ran; may be NULL).  Blocking, on the legacy default stream.  Errors:
- * SYK_EINVAL, SYK_ENOMEM, SYK_ENOCONV, SYK_ECUDA.
+ * path ran; may be NULL), *kernel_ms (may be NULL: then the step is also
+ * timed, the median of 5 launches by CUDA events).  Blocking, on the legacy
+ * default stream.  Errors: SYK_EINVAL, SYK_ENOMEM, SYK_ENOCONV, SYK_ECUDA.
  */
 int syk_tridiag_exp(int m, const double* alpha, const double* beta, double z_re, double z_im, double tol, int force_ql,
-                    double* c, double* s_acc, double* err, int* used_ql);
+                    double* c, double* s_acc, double* err, int* used_ql, double* kernel_ms);
 
 /*
  * Hardware probes for the benchmark's roofline denominators (no paper

@@ -94,7 +94,7 @@ SIGNATURES = {
     "syk_bounded_wait_selftest": (_I, [_P]),
     "syk_probe_staging": (_I, [_P, _SZ, _I, _I, C.POINTER(_D), _P]),
     "syk_probe_fp64": (_I, [C.POINTER(_D), _P]),
-    "syk_tridiag_exp": (_I, [_I, _P, _P, _D, _D, _D, _I, _P, C.POINTER(_D), C.POINTER(_D), C.POINTER(_I)]),
+    "syk_tridiag_exp": (_I, [_I, _P, _P, _D, _D, _D, _I, _P, C.POINTER(_D), C.POINTER(_D), C.POINTER(_I), _P]),
     "syk_last_error": (_I, [C.c_char_p, _SZ]),
     "syk_version": (C.c_char_p, []),
 }

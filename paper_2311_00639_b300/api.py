@@ -60,19 +60,21 @@ def probe_staging(buf, reads: int, jobs_per_cta: int = 4096, stream=None) -> flo
     return v.value
 
 
-def tridiag_exp(alpha, beta, z: complex, tol: float, force_ql: bool = False):
+def tridiag_exp(alpha, beta, z: complex, tol: float, force_ql: bool = False, timed: bool = False):
     """The Krylov engine's projected-exponential step on a given Lanczos matrix
-    (syk_tridiag_exp): returns (c complex [m], s_acc, err, used_ql)."""
+    (syk_tridiag_exp): returns (c complex [m], s_acc, err, used_ql), plus the
+    kernel time in ms (median of 5 launches) when timed."""
     a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
     b = np.ascontiguousarray(np.asarray(beta, dtype=np.float64))
     if a.shape != b.shape:
         raise ValueError("alpha and beta lengths differ")
     c = np.zeros((len(a), 2))
-    s, e, q = C.c_double(0.0), C.c_double(0.0), C.c_int(0)
+    s, e, q, ms = C.c_double(0.0), C.c_double(0.0), C.c_int(0), C.c_double(0.0)
     L.check(L.load().syk_tridiag_exp(len(a), a.ctypes.data, b.ctypes.data, float(np.real(z)), float(np.imag(z)),
                                      float(tol), int(bool(force_ql)), c.ctypes.data, C.byref(s), C.byref(e),
-                                     C.byref(q)))
-    return c[:, 0] + 1j * c[:, 1], s.value, e.value, bool(q.value)
+                                     C.byref(q), C.byref(ms) if timed else None))
+    out = (c[:, 0] + 1j * c[:, 1], s.value, e.value, bool(q.value))
+    return out + (ms.value,) if timed else out
 
 
 def probe_fp64(stream=None) -> float:

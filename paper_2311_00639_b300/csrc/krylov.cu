@@ -20,6 +20,7 @@
 #include <cmath>
 #include <algorithm>
 #include <complex>
+#include <string>
 #include <vector>
 
 #include "kernels.cuh"
@@ -280,7 +281,7 @@ KrylovResult krylov_evolve_one(const syk_terms* h, int block, double tau, double
 }  // namespace syk
 
 extern "C" int syk_tridiag_exp(int m, const double* alpha, const double* beta, double z_re, double z_im, double tol,
-                               int force_ql, double* c, double* s_acc, double* err, int* used_ql) {
+                               int force_ql, double* c, double* s_acc, double* err, int* used_ql, double* kernel_ms) {
   syk::KScalars* d = nullptr;
   int rc = SYK_OK;
   try {
@@ -303,6 +304,23 @@ extern "C" int syk_tridiag_exp(int m, const double* alpha, const double* beta, d
     syk::k_tridiag_test<<<1, 32>>>(d, m, z_re, z_im, tol, force_ql ? 0 : 1);
     SYK_CUDA(cudaGetLastError());
     SYK_CUDA(cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost));
+    if (kernel_ms) {  // median of 5 timed launches on the same input (each recomputes the step)
+      cudaEvent_t e0, e1;
+      SYK_CUDA(cudaEventCreate(&e0));
+      SYK_CUDA(cudaEventCreate(&e1));
+      std::vector<float> t(5);
+      for (auto& v : t) {
+        SYK_CUDA(cudaEventRecord(e0));
+        syk::k_tridiag_test<<<1, 32>>>(d, m, z_re, z_im, tol, force_ql ? 0 : 1);
+        SYK_CUDA(cudaEventRecord(e1));
+        SYK_CUDA(cudaEventSynchronize(e1));
+        SYK_CUDA(cudaEventElapsedTime(&v, e0, e1));
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      std::sort(t.begin(), t.end());
+      *kernel_ms = t[2];
+    }
     for (int i = 0; i < m; ++i) {
       c[2 * i] = h.c_re[i];
       c[2 * i + 1] = h.c_im[i];

@@ -6,8 +6,9 @@
 // costs about as much as 64 cycles of issue, whatever the active lanes), so
 // the default path gives every lane its own eigenvalue and eigenvector and
 // keeps each lane's work to a few O(n) recurrences:
-//   1. bisection on the Sturm count (LDL^T pivots, Wilkinson's sign rule) in
-//      FP32 locates eigenvalue k of T for lane k;
+//   1. bisection on the Sturm count (sign changes along the leading minors
+//      det(T_i - x), by their three-term recurrence) in FP32 locates
+//      eigenvalue k of T for lane k;
 //   2. Newton's method on the characteristic polynomial det(T_i - x), its
 //      three-term recurrence and derivative in FP64, polishes it, safeguarded
 //      by the Sturm count of the same recurrence (sign changes along the
@@ -42,14 +43,13 @@ __device__ inline double2 cexp_(double re, double im) {
   return make_double2(e * c, e * s);
 }
 
-// phi_1(w) = (e^w - 1) / w for complex w.
-__device__ inline double2 phi1_(double re, double im) {
-  const double a = hypot(re, im);
-  if (a < 1e-6) return make_double2(1.0 + 0.5 * re, 0.5 * im);
-  const double2 e = cexp_(re, im);
-  const double nr = e.x - 1.0, ni = e.y;
+// phi_1(w) = (e^w - 1) / w for complex w, given e = e^w.
+__device__ inline double2 phi1_(double re, double im, double2 e) {
   const double d = re * re + im * im;
-  return make_double2((nr * re + ni * im) / d, (ni * re - nr * im) / d);
+  if (d < 1e-12) return make_double2(1.0 + 0.5 * re, 0.5 * im);
+  const double nr = e.x - 1.0, ni = e.y;
+  const double r = 1.0 / d;
+  return make_double2((nr * re + ni * im) * r, (ni * re - nr * im) * r);
 }
 
 // Bits of |v| (IEEE order: for non-negative doubles, integer order = value order).
@@ -71,18 +71,50 @@ __device__ inline double warp_sum_(double v) {
   return v;
 }
 
-// Sturm count below x in FP32: the number of negative pivots of the LDL^T
-// factorisation of T - x (a zero pivot is replaced by -pivmin).
-__device__ inline int sturm_count_f32(int n, const float* df, const float* e2f, float x, float pivmin) {
-  float q = df[0] - x;
-  if (fabsf(q) < pivmin) q = -pivmin;
-  int c = q < 0.f ? 1 : 0;
-  for (int i = 1; i < n; ++i) {
-    q = (df[i] - x) - __fdiv_rn(e2f[i - 1], q);
-    if (fabsf(q) < pivmin) q = -pivmin;
-    c += q < 0.f ? 1 : 0;
+// Sign bits of two doubles / floats differ (integer test: FP64 compares
+// cost as much as FP64 arithmetic on this part).
+__device__ inline bool sign_differs(double a, double b) { return (__double2hiint(a) ^ __double2hiint(b)) < 0; }
+__device__ inline bool is_zero(double a) { return (__double_as_longlong(a) << 1) == 0; }
+
+// Sturm counts below three points x0 < x1 < x2 in FP32: sign changes along
+// det(T_i - x), i = 0..n, by the three-term recurrence on T / ||T|| (one
+// dependent FMA per row and point; the three chains share each row's loads
+// and run interleaved).  With the entries scaled to at most 1 a value grows
+// by at most 3 a row, so pairs of consecutive values are checked (and
+// rescaled by 2^-/+64 when they leave [2^-64, 2^64]) every 8 rows only.  An
+// exact zero counts as non-negative (measure zero; the FP64 stage corrects).
+__device__ inline void sturm_rescale_f32(float& p0, float& p1) {
+  const int ex = (__float_as_int(p1) >> 23) & 0xFF;
+  if (ex > 127 + 64) {
+    p0 *= 0x1p-64f;
+    p1 *= 0x1p-64f;
+  } else if (ex < 127 - 64 && ((__float_as_int(p0) >> 23) & 0xFF) < 127 - 64) {
+    p0 *= 0x1p64f;
+    p1 *= 0x1p64f;
   }
-  return c;
+}
+__device__ inline void sturm_count3_f32(int n, const float* df, const float* e2f, const float (&x)[3], int (&c)[3]) {
+  float p0[3], p1[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    p0[j] = 1.f;
+    p1[j] = df[0] - x[j];
+    c[j] = static_cast<int>(static_cast<unsigned>(__float_as_int(p1[j])) >> 31);
+  }
+  for (int i = 1; i < n; ++i) {
+    const float d = df[i], e2 = e2f[i - 1];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float p2 = fmaf(d - x[j], p1[j], -e2 * p0[j]);
+      c[j] += static_cast<int>(static_cast<unsigned>(__float_as_int(p2) ^ __float_as_int(p1[j])) >> 31);
+      p0[j] = p1[j];
+      p1[j] = p2;
+    }
+    if ((i & 7) == 7) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) sturm_rescale_f32(p0[j], p1[j]);
+    }
+  }
 }
 
 // det(T_i - x) for the leading i x i blocks by the three-term recurrence, in
@@ -97,14 +129,14 @@ struct CharPoly {
 __device__ inline CharPoly char_poly(int n, const double* d, const double* e2, double x) {
   double p0 = 1.0, dp0 = 0.0;
   double p1 = d[0] - x, dp1 = -1.0;
-  if (p1 == 0.0) p1 = -0x1p-900;
-  int below = p1 < 0.0 ? 1 : 0;
+  if (is_zero(p1)) p1 = -0x1p-900;
+  int below = __double2hiint(p1) < 0 ? 1 : 0;
   for (int i = 1; i < n; ++i) {
     const double a = d[i] - x;
     double p2 = fma(a, p1, -e2[i - 1] * p0);
     const double dp2 = fma(a, dp1, -fma(e2[i - 1], dp0, p1));
-    if (p2 == 0.0) p2 = (p1 < 0.0 ? 0x1p-900 : -0x1p-900) * fabs(p1);
-    below += ((p2 < 0.0) != (p1 < 0.0)) ? 1 : 0;
+    if (is_zero(p2)) p2 = -0x1p-300 * p1;  // a zero counts as a sign change
+    below += sign_differs(p2, p1) ? 1 : 0;
     p0 = p1;
     dp0 = dp1;
     p1 = p2;
@@ -135,53 +167,70 @@ __device__ bool eig_lane_parallel(const KScalars* sc, int n, double (*Z)[kMaxKry
   __shared__ double sd[kMaxKrylov], se[kMaxKrylov], se2[kMaxKrylov], sinv[kMaxKrylov];
   __shared__ float sdf[kMaxKrylov], se2f[kMaxKrylov];
   const int lane = threadIdx.x & 31;
-  double glo = 1e300, ghi = -1e300, emax2 = 0.0;
+  // Gershgorin interval in FP32, widened by 2^-16 relative (it only brackets)
+  float glf = 3e38f, ghf = -3e38f;
   for (int i = lane; i < n; i += 32) {
     const double di = sc->alpha[i];
     const double ei = i < n - 1 ? sc->beta[i] : 0.0;
-    const double ep = i > 0 ? sc->beta[i - 1] : 0.0;
+    const float ep = i > 0 ? static_cast<float>(sc->beta[i - 1]) : 0.f;
     sd[i] = di;
     se[i] = ei;
     se2[i] = ei * ei;
     sinv[i] = i < n - 1 ? 1.0 / ei : 0.0;
-    sdf[i] = static_cast<float>(di);
-    se2f[i] = static_cast<float>(ei * ei);
-    glo = fmin(glo, di - fabs(ei) - fabs(ep));  // Gershgorin
-    ghi = fmax(ghi, di + fabs(ei) + fabs(ep));
-    emax2 = fmax(emax2, ei * ei);
+    const float df = static_cast<float>(di), ef = fabsf(static_cast<float>(ei)) + fabsf(ep);
+    glf = fminf(glf, df - ef);
+    ghf = fmaxf(ghf, df + ef);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
-    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
-    emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
+    glf = fminf(glf, __shfl_xor_sync(0xffffffffu, glf, o));
+    ghf = fmaxf(ghf, __shfl_xor_sync(0xffffffffu, ghf, o));
   }
   __syncwarp();
+  const float padf = 0x1p-16f * fmaxf(fabsf(glf), fabsf(ghf));
+  const double glo = static_cast<double>(glf - padf), ghi = static_cast<double>(ghf + padf);
   const double tnorm = fmax(fabs(glo), fabs(ghi));
   const double width = ghi - glo;
   if (!(width > 0.0) || !(tnorm < 1e300)) return false;
-  const float pivmin = static_cast<float>(fmax(1.0, emax2) * 1e-30);
-  const double eps = 0x1p-52;
+  const double rn = 1.0 / tnorm;  // the FP32 bracketing works on T / ||T||
+  for (int i = lane; i < n; i += 32) {
+    sdf[i] = static_cast<float>(sd[i] * rn);
+    se2f[i] = static_cast<float>(se2[i] * rn * rn);
+  }
+  __syncwarp();
   bool ok = true;
   for (int slot = 0; slot < 2; ++slot) {
     const int k = lane + 32 * slot;
     if (slot == 1 && n <= 32) break;
     double xk = 0.0;
     if (k < n) {
-      // 1. FP32 bisection for the k-th eigenvalue (0-based, ascending)
-      float a = static_cast<float>(glo - 1e-6 * width), b = static_cast<float>(ghi + 1e-6 * width);
-      for (int it = 0; it < 30; ++it) {
-        const float mid = 0.5f * (a + b);
-        if (!(mid > a && mid < b)) break;
-        if (sturm_count_f32(n, sdf, se2f, mid, pivmin) > k)
-          b = mid;
-        else
-          a = mid;
+      // 1. FP32 bracketing of the k-th eigenvalue (0-based, ascending): the
+      //    interval [a, b] (count(a) <= k < count(b)) is cut in four per
+      //    round by three Sturm counts at once, down to FP32 resolution
+      float a = static_cast<float>((glo - 1e-6 * width) * rn), b = static_cast<float>((ghi + 1e-6 * width) * rn);
+      for (int it = 0; it < 16; ++it) {
+        const float w = b - a;
+        const float xs3[3] = {a + 0.25f * w, a + 0.5f * w, a + 0.75f * w};
+        if (!(xs3[0] > a && xs3[2] < b && xs3[0] < xs3[1] && xs3[1] < xs3[2])) break;
+        int cnt[3];
+        sturm_count3_f32(n, sdf, se2f, xs3, cnt);
+        if (cnt[0] > k) {
+          b = xs3[0];
+        } else if (cnt[1] > k) {
+          a = xs3[0];
+          b = xs3[1];
+        } else if (cnt[2] > k) {
+          a = xs3[1];
+          b = xs3[2];
+        } else {
+          a = xs3[2];
+        }
       }
       // 2. FP64 Newton on det(T - x), bracketed by the Sturm count
-      double A = static_cast<double>(a) - 4.0 * (static_cast<double>(b) - a) - 1e-6 * width;
-      double B = static_cast<double>(b) + 4.0 * (static_cast<double>(b) - a) + 1e-6 * width;
-      double x = 0.5 * (static_cast<double>(a) + static_cast<double>(b));
+      const double af = static_cast<double>(a) * tnorm, bf = static_cast<double>(b) * tnorm;
+      double A = af - 4.0 * (bf - af) - 1e-6 * width;
+      double B = bf + 4.0 * (bf - af) + 1e-6 * width;
+      double x = 0.5 * (af + bf);
       bool conv = false;
       for (int it = 0; it < 12 && !conv; ++it) {
         const CharPoly cp = char_poly(n, sd, se2, x);
@@ -191,8 +240,10 @@ __device__ bool eig_lane_parallel(const KScalars* sc, int n, double (*Z)[kMaxKry
           A = x;
         // a Newton step at rounding level ends the iteration (the iterate may
         // then sit on the bracket's end, where the count put it)
-        const double step = (cp.dp != 0.0) ? cp.p / cp.dp : 1e300;
-        if (fabs(step) <= 4.0 * eps * fmax(fabs(x), 1e-3 * tnorm)) {
+        const double step = !is_zero(cp.dp) ? cp.p / cp.dp : 1e300;
+        // Newton converges quadratically here: after a step below 2^-36 of the
+        // scale the error is of order step^2 / gap, far below rounding
+        if (fabs(step) <= 0x1p-36 * fmax(fabs(x), 1e-3 * tnorm)) {
           conv = true;
           x -= step;
           break;
@@ -204,67 +255,61 @@ __device__ bool eig_lane_parallel(const KScalars* sc, int n, double (*Z)[kMaxKry
       ok = ok && conv;
       xk = x;
       // 3. eigenvector: x_i from the top (x_0 = 1), y_i from the bottom
-      //    (y_{n-1} = 1), stored with a power-of-two scale count each
+      //    (y_{n-1} = 1).  When a value passes 2^600 the values stored so far
+      //    are scaled by 2^-600 with it (rare; earlier entries may underflow
+      //    to zero, they are negligible then).  The backward sweep picks the
+      //    join row r maximising |x_r y_r| from binary exponents on the fly.
       double xv[kMaxKrylov], yv[kMaxKrylov];
-      int xs[kMaxKrylov], ys[kMaxKrylov];
       {
         double u0 = 0.0, u1 = 1.0;
-        int sc_ = 0;
         xv[0] = 1.0;
-        xs[0] = 0;
         for (int i = 0; i + 1 < n; ++i) {
           double u2 = fma(x - sd[i], u1, -(i > 0 ? se[i - 1] : 0.0) * u0) * sinv[i];
-          if (exp2_of(u2) > 600 && u2 != 0.0) {
+          if (exp2_of(u2) > 600) {
             u2 *= 0x1p-600;
             u1 *= 0x1p-600;
-            ++sc_;
+            for (int j = 0; j <= i; ++j) xv[j] *= 0x1p-600;
           }
           xv[i + 1] = u2;
-          xs[i + 1] = sc_;
           u0 = u1;
           u1 = u2;
         }
       }
+      auto expsum = [](double a, double b) {
+        return (is_zero(a) || is_zero(b)) ? -100000 : exp2_of(a) + exp2_of(b);
+      };
+      int r = n - 1;
+      int best = expsum(xv[n - 1], 1.0);
       {
         double u0 = 0.0, u1 = 1.0;
-        int sc_ = 0;
         yv[n - 1] = 1.0;
-        ys[n - 1] = 0;
         for (int i = n - 1; i > 0; --i) {
           double u2 = fma(x - sd[i], u1, -(i < n - 1 ? se[i] : 0.0) * u0) * sinv[i - 1];
-          if (exp2_of(u2) > 600 && u2 != 0.0) {
+          if (exp2_of(u2) > 600) {
             u2 *= 0x1p-600;
             u1 *= 0x1p-600;
-            ++sc_;
+            for (int j = i; j < n; ++j) yv[j] *= 0x1p-600;
+            best -= 600;
           }
           yv[i - 1] = u2;
-          ys[i - 1] = sc_;
           u0 = u1;
           u1 = u2;
-        }
-      }
-      // join at the row r maximising |x_r y_r| (scale counts included)
-      int r = 0;
-      int best = -0x7FFFFFFF;
-      for (int i = 0; i < n; ++i) {
-        const double pr = xv[i] * yv[i];
-        const int e = (pr != 0.0 ? exp2_of(pr) : -5000) + 600 * (xs[i] + ys[i]);
-        if (e > best) {
-          best = e;
-          r = i;
+          const int e = expsum(xv[i - 1], u2);
+          if (e > best) {
+            best = e;
+            r = i - 1;
+          }
         }
       }
       const double ixr = 1.0 / xv[r], iyr = 1.0 / yv[r];
       double nrm = 0.0;
       for (int i = 0; i < n; ++i) {
-        const int ds = (i <= r) ? xs[i] - xs[r] : ys[i] - ys[r];  // <= 0
-        double v = (i <= r) ? xv[i] * ixr : yv[i] * iyr;
-        if (ds != 0) v = ds < -1 ? 0.0 : v * 0x1p-600;
-        xv[i] = v;
+        const double v = (i <= r) ? xv[i] * ixr : yv[i] * iyr;
         nrm = fma(v, v, nrm);
       }
       const double inv = rsqrt(nrm);
-      for (int i = 0; i < n; ++i) Z[i][k] = xv[i] * inv;
+      const double fx = ixr * inv, fy = iyr * inv;
+      for (int i = 0; i < n; ++i) Z[i][k] = (i <= r) ? xv[i] * fx : yv[i] * fy;
     }
     lam[slot] = xk;
   }
@@ -275,10 +320,10 @@ __device__ bool eig_lane_parallel(const KScalars* sc, int n, double (*Z)[kMaxKry
   // step uses c = sum_k f(lam_k) z_k z_k[0]; errors of nearly equal lam_k
   // (whose vectors mix) enter c as these two sums do, so passing them bounds
   // the eigenvector part of the error of c.
-  __shared__ double slam[kMaxKrylov];
+  __shared__ double szl[kMaxKrylov];  // lam_k z_k[0]
   for (int slot = 0; slot < 2; ++slot) {
     const int k = lane + 32 * slot;
-    if (k < n) slam[k] = lam[slot];
+    if (k < n) szl[k] = lam[slot] * Z[0][k];
   }
   __syncwarp();
   const double next0 = __shfl_down_sync(0xffffffffu, lam[0], 1);
@@ -293,9 +338,8 @@ __device__ bool eig_lane_parallel(const KScalars* sc, int n, double (*Z)[kMaxKry
     if (i < n) {
       double s0 = 0.0, s1 = 0.0;
       for (int k = 0; k < n; ++k) {
-        const double w = Z[i][k] * Z[0][k];
-        s0 += w;
-        s1 = fma(w, slam[k], s1);
+        s0 = fma(Z[i][k], Z[0][k], s0);
+        s1 = fma(Z[i][k], szl[k], s1);
       }
       const double t0 = i == 0 ? 1.0 : 0.0;
       const double t1 = i == 0 ? sd[0] : (i == 1 ? se[0] : 0.0);
@@ -396,7 +440,7 @@ __device__ void substep_search(KScalars* sc, int n, int m, double resid, double 
       const double w0 = Z[0][k];
       const double dk = lam[slot];
       const double2 ex = cexp_(-hr * dk, -hi * dk);
-      const double2 ph = phi1_(-hr * dk, -hi * dk);
+      const double2 ph = phi1_(-hr * dk, -hi * dk, ex);
       Er[k] = ex.x * w0;
       Ei[k] = ex.y * w0;
       Pr[k] = ph.x * w0;
@@ -404,7 +448,6 @@ __device__ void substep_search(KScalars* sc, int n, int m, double resid, double 
     }
     __syncwarp();
     double cr0 = 0, ci0 = 0, cr1 = 0, ci1 = 0;  // rows lane, lane+32
-    double pr_last = 0, pi_last = 0;
     for (int k = 0; k < n; ++k) {
       const double er = Er[k], ei = Ei[k];
       if (lane < n) {
@@ -415,9 +458,15 @@ __device__ void substep_search(KScalars* sc, int n, int m, double resid, double 
         cr1 += Z[lane + 32][k] * er;
         ci1 += Z[lane + 32][k] * ei;
       }
+    }
+    // last row of phi_1(-hT) e_1: each lane its own eigenvalues' terms, then a warp sum
+    double pr_last = 0, pi_last = 0;
+    for (int k = lane; k < n; k += 32) {
       pr_last += Z[n - 1][k] * Pr[k];
       pi_last += Z[n - 1][k] * Pi[k];
     }
+    pr_last = warp_sum_(pr_last);
+    pi_last = warp_sum_(pi_last);
     __syncwarp();
     const double nc = sqrt(warp_sum_(cr0 * cr0 + ci0 * ci0 + cr1 * cr1 + ci1 * ci1));
     // |c_{n-1}|: owned by lane (n-1) % 32 in slot (n-1) / 32.

@@ -1,7 +1,7 @@
 """Continuous-batching OTOC server over the batched engine (syk_batch_*).
 
-Requests (one disorder realisation each: N, k, beta, time grid, seeds) arrive
-over time.  The loop compiles each arriving request's Hamiltonian
+Requests (one disorder realisation each: N, couplings, beta, time grid,
+seeds) arrive over time.  The loop compiles each arriving request's Hamiltonian
 (syk_build_terms), admits it into the running batch as soon as a slot and
 enough arena memory are free (admission by device footprint), advances all
 admitted jobs a few ticks at a time, and retires finished ones — so requests
@@ -71,12 +71,15 @@ class OtocServer:
     """batch / make_terms can be injected (tests drive the scheduling with fakes)."""
 
     def __init__(self, dtype: str = "c64", max_slots: int = 256, hbm_budget_bytes: int = 8 << 30, m: int = 30,
-                 tol=None, ticks_per_step: int = 4, batch=None, make_terms=None):
+                 tol=None, ticks_per_step: int = 4, batch=None, make_terms=None, policy: str = "fifo"):
         self.batch = batch if batch is not None else Batch(dtype=dtype, max_slots=max_slots,
                                                            max_bytes=hbm_budget_bytes, m=m, tol=tol)
         self.make_terms = make_terms if make_terms is not None else (
             lambda r: Terms(r.N, r.quads, r.J, dtype=dtype))
         self.ticks = ticks_per_step
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy must be 'fifo' or 'sjf'")
+        self.policy = policy
         self.live = {}  # rid -> (Request, Terms, admitted time)
 
     def close(self):
@@ -89,7 +92,7 @@ class OtocServer:
         """Serve the requests (arrival times in seconds from now); returns the
         Results in completion order."""
         pending = sorted(requests, key=lambda r: r.arrival)
-        queue = []  # arrived and compiled, waiting for admission (FIFO, no overtaking)
+        queue = []  # arrived and compiled, waiting for admission (FIFO without overtaking, or SJF)
         out = []
         t0 = clock()
         now = lambda: clock() - t0
@@ -99,6 +102,8 @@ class OtocServer:
             while i < len(pending) and pending[i].arrival <= t:
                 queue.append((pending[i], self.make_terms(pending[i])))
                 i += 1
+            if self.policy == "sjf":  # shortest estimated work first (stable for equal work)
+                queue.sort(key=lambda rh: work_estimate(rh[0], rh[1]))
             while queue:
                 r, h = queue[0]
                 a = r.a if r.a >= 0 else r.N + r.a
@@ -118,31 +123,19 @@ class OtocServer:
         return out
 
 
+def work_estimate(r: Request, h) -> float:
+    """Term x amplitude updates of a request, up to a common factor: its
+    matvecs grow like the sum over the grid of |t| (the ket chain evolves
+    by t at every point), each costing terms x D."""
+    nterms = getattr(h, "n_terms", len(r.J))
+    D = getattr(h, "D", 1 << (r.N // 2 - 1))
+    t = np.asarray(r.t_grid, dtype=np.float64)
+    return float(nterms) * float(D) * float(len(t) + np.sum(np.abs(t)))
+
+
 def summarize(results, wall: float) -> dict:
     lat = [r.latency for r in results]
     return {"requests": len(results), "wall_s": wall, "realizations_per_s": len(results) / wall if wall > 0 else None,
             "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
             "mean_latency_s": float(np.mean(lat)) if lat else None,
             "failed": sum(1 for r in results if r.status != 0)}
-
-
-def served_workload(n: int, rate: float, seed: int = 0, n_choices=(28, 30, 32, 34, 36, 38, 40, 42, 44, 46, 48),
-                    weight: float = 0.7, ks=(0.5, 1.0, 2.0, 4.0), betas=(2.0, 5.0, 10.0, 20.0), t_max: float = 20.0,
-                    dt: float = 0.1):
-    """The served configuration: N weighted toward small sizes (P(N) ~ weight^((N-28)/2)),
-    k and beta uniform over the listed values, t = 0..t_max step dt, Poisson arrivals."""
-    import syk_inputs as si
-
-    rng = np.random.default_rng(seed)
-    Ns = np.asarray(n_choices)
-    p = weight ** ((Ns - Ns[0]) / 2.0)
-    p /= p.sum()
-    arr = poisson_arrivals(n, rate, seed)
-    grid = np.round(np.arange(0.0, t_max + 1e-9, dt), 10)
-    reqs = []
-    for i in range(n):
-        N = int(rng.choice(Ns, p=p))
-        k = float(rng.choice(ks))
-        q, J, _ = si.sample_sparse_syk(N, k, seed=10_000 + seed * 100_000 + i)
-        reqs.append(Request(i, float(arr[i]), N, q, J, float(rng.choice(betas)), grid, seed=seed * 1_000_003 + i))
-    return reqs

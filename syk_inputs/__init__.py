@@ -44,6 +44,7 @@ __all__ = [
     "pauli_mask",
     "heisenberg_chain",
     "random_pauli_terms",
+    "served_requests",
 ]
 
 
@@ -225,3 +226,26 @@ def random_pauli_terms(L: int, T: int, seed: int, max_weight: int = 4):
         xs.append(x)
         zs.append(z)
     return np.array(xs, dtype=np.uint32), np.array(zs, dtype=np.uint32), rng.normal(size=T)
+
+
+def served_requests(n: int, rate: float, seed: int = 0, n_choices=(28, 30, 32, 34, 36, 38, 40, 42, 44, 46, 48),
+                    weight: float = 0.7, ks=(0.5, 1.0, 2.0, 4.0), betas=(2.0, 5.0, 10.0, 20.0), t_max: float = 20.0,
+                    dt: float = 0.1):
+    """The served workload: n requests with Poisson arrival times of the given
+    rate (1/s), N weighted toward small sizes (P(N) ~ weight^((N - N_min)/2)),
+    sparsity k and beta uniform over the listed values, t = 0..t_max step dt.
+    Returns dicts with keys rid, arrival, N, quads, J, beta, t_grid, seed."""
+    rng = np.random.default_rng(seed)
+    Ns = np.asarray(n_choices)
+    p = weight ** ((Ns - Ns[0]) / 2.0)
+    p /= p.sum()
+    arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=n))
+    grid = np.round(np.arange(0.0, t_max + 1e-9, dt), 10)
+    out = []
+    for i in range(n):
+        N = int(rng.choice(Ns, p=p))
+        k = float(rng.choice(ks))
+        q, J, _ = sample_sparse_syk(N, k, seed=10_000 + seed * 100_000 + i)
+        out.append({"rid": i, "arrival": float(arr[i]), "N": N, "quads": q, "J": J, "beta": float(rng.choice(betas)),
+                    "t_grid": grid, "seed": seed * 1_000_003 + i})
+    return out

@@ -75,6 +75,29 @@ def test_fifo_admission_limits_and_latency():
     assert s["requests"] == 40 and s["p99_latency_s"] >= s["p50_latency_s"] > 0
 
 
+def test_sjf_admission_prefers_short_requests():
+    """With every request waiting at t = 0 and one slot, SJF admits in order of
+    estimated work (terms x D x (points + sum |t|)); equal work keeps arrival
+    order.  FIFO admits in arrival order."""
+    grids = [np.linspace(0, 8, 9), np.linspace(0, 1, 2), np.linspace(0, 4, 5), np.linspace(0, 1, 2)]
+    reqs = [serve.Request(i, 0.0, 10, None, np.zeros(5), 1.0, grids[i], seed=i) for i in range(4)]
+    order = {}
+    for policy in ("fifo", "sjf"):
+        fb = FakeBatch(slots=1, budget=2 ** 10)
+        t = [0.0]
+
+        def clock():
+            t[0] += 1e-4
+            return t[0]
+
+        srv = serve.OtocServer(batch=fb, make_terms=FakeTerms, ticks_per_step=2, policy=policy)
+        res = srv.run(reqs, clock=clock, sleep=lambda s: None)
+        assert sorted(r.rid for r in res) == [0, 1, 2, 3]
+        order[policy] = fb.admitted_order
+    assert order["fifo"] == [0, 1, 2, 3]
+    assert order["sjf"] == [1, 3, 2, 0]
+
+
 def test_poisson_and_percentiles():
     arr = serve.poisson_arrivals(20000, rate=50.0, seed=1)
     gaps = np.diff(np.concatenate([[0.0], arr]))
@@ -86,9 +109,13 @@ def test_poisson_and_percentiles():
 
 
 def test_served_workload_distribution():
-    reqs = serve.served_workload(300, rate=10.0, seed=2, t_max=1.0, dt=0.5)
-    Ns = np.array([r.N for r in reqs])
+    import syk_inputs as si
+
+    reqs = si.served_requests(300, rate=10.0, seed=2, t_max=1.0, dt=0.5)
+    Ns = np.array([r["N"] for r in reqs])
     assert Ns.min() >= 28 and Ns.max() <= 48 and np.all(Ns % 2 == 0)
     assert np.mean(Ns == 28) > np.mean(Ns == 34) > 0  # weighted toward small N
-    assert {r.beta for r in reqs} <= {2.0, 5.0, 10.0, 20.0}
-    assert np.allclose(reqs[0].t_grid, [0.0, 0.5, 1.0])
+    assert {r["beta"] for r in reqs} <= {2.0, 5.0, 10.0, 20.0}
+    assert np.allclose(reqs[0]["t_grid"], [0.0, 0.5, 1.0])
+    arr = np.array([r["arrival"] for r in reqs])
+    assert np.allclose(arr, serve.poisson_arrivals(300, rate=10.0, seed=2))
