@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--k", type=float, default=4.0)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-relabel", action="store_true",
+                    help="use the identity Jordan-Wigner order instead of the locality-ordered labels")
+    ap.add_argument("--no-identity", action="store_true",
+                    help="skip the comparison timing of the identity Jordan-Wigner order")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-l2", action="store_true")
@@ -84,9 +88,21 @@ def parse():
 
 
 def workload_config(args, T):
+    rep = ("jw, Majoranas relabelled for locality (syk_relabel_majoranas)" if not getattr(args, "no_relabel", False)
+           else "jw")
     return {"workload": f"sparse SYK H·psi, N={args.N}, k={args.k:g}, one parity block",
-            "N": args.N, "k": args.k, "terms": T, "D": 1 << (args.N // 2 - 1), "rep": "jw",
+            "N": args.N, "k": args.k, "terms": T, "D": 1 << (args.N // 2 - 1), "rep": rep,
             "states": 1, "l2": "inputs larger than L2 (16 GiB per vector), no flush"}
+
+
+def locality_terms(syk, N, q, J, args):
+    """The benchmark Hamiltonian in the library's locality-ordered
+    Jordan-Wigner labels (the same operator up to a unitary change of basis;
+    fewer staged input tiles per output tile), unless --no-relabel."""
+    if getattr(args, "no_relabel", False):
+        return q, J, None
+    r = syk.relabel_for_locality(N, q, J)
+    return r["quads"], r["J"], {"patterns_before": r["patterns_before"], "patterns_after": r["patterns_after"]}
 
 
 # ------------------------------------------------------------------ clocks --
@@ -736,7 +752,8 @@ def ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     barrier = (lambda: dist.barrier()) if dist else (lambda: None)
 
-    q, J = replica_terms(si, args.N, args.k, rank)
+    q0, J0 = replica_terms(si, args.N, args.k, rank)
+    q, J, relabel_info = locality_terms(syk, args.N, q0, J0, args)
     h = syk.Terms(args.N, q, J, dtype="c64")
     T, D = h.n_terms, h.D
     psi, _ = h.random_state(seed=1234, state_id=rank, blocks=(0,))
@@ -753,6 +770,18 @@ def ours(args):
     dt = max_over_ranks(dt, dist)
     per_step = dt / args.steps
     value = world * T * D * args.steps / dt / 1e9
+
+    # the same step with the identity Jordan-Wigner order (for comparison)
+    identity = None
+    if relabel_info is not None and not args.no_identity:
+        h0 = syk.Terms(args.N, q0, J0, dtype="c64")
+        k0 = max(3, min(5, args.steps))
+        d0 = max_over_ranks(time_matvecs(h0, psi, out, k0, 2, torch), dist)
+        identity = {"value": world * T * D * k0 / d0 / 1e9, "unit": UNIT, "ms_per_step": d0 * 1e3 / k0,
+                    "passes": h0.info["n_passes"], "tile_reads": h0.info["n_tile_reads"],
+                    "note": "identity Jordan-Wigner order, same couplings (not the timed value)"}
+        h0.close()
+        relabel_info.update({"passes": h.info["n_passes"], "tile_reads": h.info["n_tile_reads"]})
 
     # e2e through the public API: every step copies its input psi from pinned
     # host memory to the device, applies H (syk_apply_H) and copies the result
@@ -938,7 +967,8 @@ def ours(args):
                 "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 states)", "data": "synthetic",
                 "config": {**workload_config(args, T), "parallelism": f"replicas x{world}",
-                           "matvec_passes": h.info["n_passes"]},
+                           "matvec_passes": h.info["n_passes"], "relabel": relabel_info},
+                "jw_identity_order": identity,
                 "gpu_launches": args.steps * h.info["n_passes"], "roofline": roof, "roofline_l2_staging": roof_l2,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "fp64": fp64, "clocks": clk, "gpu": props.name, "otoc_batched": batched, "otoc_served": served,
@@ -961,6 +991,7 @@ def otoc_only(args):
         # basis of m+1 = 11 vectors (4 + 11 vectors of 16 GiB live; --n64-two-pass keeps 3
         # by regenerating the basis), beta=10, one Philox state, t in {0, 0.5}; both blocks.
         q, J, _ = si.sample_sparse_syk(args.N, args.k, r=0)
+        q, J, _ = locality_terms(syk, args.N, q, J, args)  # keeps Majoranas N-1, N-2 (the OTOC's) in place
         h = syk.Terms(args.N, q, J, dtype="c64")
         grid = [0.0, 0.5]
         torch.cuda.synchronize()

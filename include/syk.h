@@ -543,6 +543,36 @@ int syk_otoc_exact_trace_batched(const syk_terms_t* h, int n_pairs, const int32_
 int syk_bounded_wait_selftest(syk_stream_t stream);
 
 /*
+ * syk_relabel_majoranas — a Jordan-Wigner ordering of the Majoranas that
+ * lowers the number of distinct flip patterns above the matvec tile, i.e.
+ * the input tiles the complex64 H psi stages per output tile (the paper has
+ * no counterpart: its representation is Eq. (S1)).  A relabelling of the
+ * Majoranas is an automorphism of the Clifford algebra, implemented by a
+ * unitary on the state space, so the spectrum of H and the exact-trace OTOC
+ * of Eq. (2) do not change; single states are expressed in the new basis.
+ *   quads, J   : HOST, as for syk_build_terms (N Majoranas, T terms).
+ *   tile_bits  : amplitude bits inside a tile (11 for this library's kernels).
+ *   iterations : simulated-annealing moves (swaps of two Majoranas between
+ *                qubits; e.g. 200000); seed: the moves' random seed
+ *                (deterministic for a given seed).
+ *   perm       : HOST int32 [N] out: physical Majorana i becomes Jordan-Wigner
+ *                Majorana perm[i]; Majoranas N-2 and N-1 keep the top qubit
+ *                (perm[N-2] = N-2, perm[N-1] = N-1), so chi_{N-1}, chi_{N-2}
+ *                stay diagonal between the parity blocks.
+ *   quads_out, J_out : HOST [T][4], [T] out (may be NULL): the same
+ *                Hamiltonian in the new labels, each quadruple sorted and its
+ *                coupling multiplied by the sign of the sorting permutation
+ *                (distinct Majoranas anticommute); pass them to
+ *                syk_build_terms with SYK_REP_JW.
+ *   patterns_before / after : HOST, may be NULL: distinct patterns of the
+ *                identity ordering and of the returned one.
+ * Host-only (no CUDA call).  Errors: SYK_EINVAL.
+ */
+int syk_relabel_majoranas(int N, int64_t T, const int32_t* quads, const double* J, int tile_bits, int64_t iterations,
+                          uint64_t seed, int32_t* perm, int32_t* quads_out, double* J_out, int64_t* patterns_before,
+                          int64_t* patterns_after);
+
+/*
  * syk_tridiag_exp — the projected-exponential step of the Krylov engine on a
  * caller's Lanczos matrix (supplement Sec. I.A, the Krylov time evolution;
  * exposed for testing): T = tridiag(beta[0..m-2], alpha[0..m-1],

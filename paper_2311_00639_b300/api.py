@@ -60,6 +60,24 @@ def probe_staging(buf, reads: int, jobs_per_cta: int = 4096, stream=None) -> flo
     return v.value
 
 
+def relabel_for_locality(N: int, quads, J, iterations: int = 200000, seed: int = 1, tile_bits: int = 11):
+    """A Jordan-Wigner ordering of the Majoranas with fewer distinct flip
+    patterns above the matvec tile (syk_relabel_majoranas).  Returns
+    {"perm", "quads", "J", "patterns_before", "patterns_after"}: physical
+    Majorana i is Jordan-Wigner Majorana perm[i]; quads / J are the same
+    Hamiltonian in the new labels (for Terms(N, quads, J)); perm[N-2] = N-2
+    and perm[N-1] = N-1."""
+    q, j = _host_arrays(quads, J)
+    perm = np.zeros(N, np.int32)
+    qo = np.zeros_like(q)
+    jo = np.zeros_like(j)
+    b, a = C.c_int64(0), C.c_int64(0)
+    L.check(L.load().syk_relabel_majoranas(N, q.shape[0], q.ctypes.data, j.ctypes.data, int(tile_bits),
+                                           int(iterations), C.c_uint64(seed), perm.ctypes.data, qo.ctypes.data,
+                                           jo.ctypes.data, C.byref(b), C.byref(a)))
+    return {"perm": perm, "quads": qo, "J": jo, "patterns_before": b.value, "patterns_after": a.value}
+
+
 def tridiag_exp(alpha, beta, z: complex, tol: float, force_ql: bool = False, timed: bool = False):
     """The Krylov engine's projected-exponential step on a given Lanczos matrix
     (syk_tridiag_exp): returns (c complex [m], s_acc, err, used_ql), plus the

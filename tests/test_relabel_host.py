@@ -1,0 +1,57 @@
+"""syk_relabel_majoranas (host, no GPU): the Jordan-Wigner reordering of the
+Majoranas that lowers the complex64 matvec's staged tiles.  A relabelling is
+an automorphism of the Clifford algebra, so the relabelled Hamiltonian must
+have the original spectrum and the original exact-trace OTOC (the oracle
+computes both, for the original and the relabelled couplings); the search
+must keep chi_{N-2}, chi_{N-1} on the top qubit, be deterministic, and on the
+N = 64 benchmark instance cut the distinct flip patterns (staged tiles)."""
+import numpy as np
+
+import syk_inputs as si
+from oracle import hamiltonian as ham
+from oracle import majorana as mj
+from oracle import otoc as ot
+
+
+def relabel(N, q, J, **kw):
+    import paper_2311_00639_b300 as syk
+
+    return syk.relabel_for_locality(N, q, J, **kw)
+
+
+def test_relabelled_hamiltonian_is_unitarily_equivalent():
+    N = 12
+    q, J, _ = si.sample_sparse_syk(N, 6, r=2)
+    r = relabel(N, q, J, iterations=20000, tile_bits=2)
+    perm = r["perm"]
+    assert sorted(perm.tolist()) == list(range(N))
+    assert perm[N - 2] == N - 2 and perm[N - 1] == N - 1
+    assert np.all(np.diff(r["quads"], axis=1) > 0)
+    H0 = ham.dense_H(N, q, J, "jw")
+    H1 = ham.dense_H(N, r["quads"], r["J"], "jw")
+    assert np.allclose(np.linalg.eigvalsh(H0), np.linalg.eigvalsh(H1), atol=1e-12)
+    X = mj.chis(N, "jw")
+    ts = [0.0, 1.0, 2.5]
+    F0 = ot.F_trace(H0, X, N - 1, N - 2, 2.0, ts)
+    F1 = ot.F_trace(H1, X, perm[N - 1], perm[N - 2], 2.0, ts)
+    assert np.max(np.abs(F0 - F1)) < 1e-12
+    # another pair of Majoranas, relabelled
+    F0 = ot.F_trace(H0, X, 3, 8, 1.0, ts)
+    F1 = ot.F_trace(H1, X, perm[3], perm[8], 1.0, ts)
+    assert np.max(np.abs(F0 - F1)) < 1e-12
+
+
+def test_relabel_is_deterministic_and_cuts_patterns_at_N64():
+    import paper_2311_00639_b300 as syk
+
+    N = 64
+    q, J, _ = si.sample_sparse_syk(N, 4, r=0)
+    a = relabel(N, q, J, iterations=50000)
+    b = relabel(N, q, J, iterations=50000)
+    assert np.array_equal(a["perm"], b["perm"]) and np.array_equal(a["J"], b["J"])
+    assert a["patterns_after"] <= 0.75 * a["patterns_before"]
+    p0 = syk.plan_host(N, q, J, dtype="c64")
+    p1 = syk.plan_host(N, a["quads"], a["J"], dtype="c64")
+    assert p1["n_runs"] < 0.75 * p0["n_runs"]
+    # the same couplings up to sign, term by term
+    assert np.allclose(np.abs(a["J"]), np.abs(J))
