@@ -301,9 +301,26 @@ def reference_arm(args):
 KERNEL_SOURCES = ("apply.cu", "tma_common.cuh", "device_common.cuh", "plan.cpp", "records.cpp", "capi.cu", "internal.h")
 
 
-def measured_traffic(T, D):
-    """DRAM bytes per matvec from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def plan_dram_model(syk, N, q, J):
+    """DRAM bytes per H psi predicted from the pass plan: every pass reads its
+    input once (its super-tiles stay in L2 for the pass's terms) and writes the
+    output once, passes after the first also read the partial sum, and each
+    straggler term reads its input tiles from DRAM."""
+    pl = syk.plan_host(N, q, J, dtype="c64")
+    D = 1 << (N // 2 - 1)
+    read = write = 0
+    for i, p in enumerate(pl["passes"]):
+        strag = int(pl["straggler"][p["t0"]:p["t1"]].sum())
+        read += 8 * D * (1 + (1 if i > 0 else 0) + strag)
+        write += 8 * D
+    return read, write
+
+
+def measured_traffic(syk, N, q, J):
+    """DRAM bytes per H psi: the plan model for this Hamiltonian times the
+    ratio measured / modelled of the committed small-case ncu capture (N=56,
+    1 GiB vectors), if that capture was taken on the current kernel, planner
+    and record sources (else None)."""
     import hashlib
 
     try:
@@ -313,8 +330,8 @@ def measured_traffic(T, D):
             h.update(open(os.path.join(ROOT, "paper_2311_00639_b300", "csrc", f), "rb").read())
         if rec.get("kernel_sources_sha256") != h.hexdigest():
             return None
-        # scale the captured size to this one by term x amplitude work
-        return rec["dram_bytes_per_matvec"] * (T * D) / (rec["terms"] * rec["D"])
+        r, w = plan_dram_model(syk, N, q, J)
+        return (r + w) * rec["measured_over_model"]
     except Exception:
         return None
 
@@ -912,7 +929,7 @@ def ours(args):
             "tile_reads": h.info["n_tile_reads"], "staged_GBps": staged_gbps,
             "l2_resident_ceiling": l2res,
             "frac_of_l2_resident": staged_gbps / l2res["staged_GBps"] if l2res else None}
-    roof["traffic"] = measured_traffic(T, D)
+    roof["traffic"] = measured_traffic(syk, args.N, q, J)
     # The binding limit of this kernel: every term x amplitude needs its own
     # 8-byte input from L2 (terms of a pass that read the same tile share one
     # staged copy), so the L2 -> shared-memory staging rate bounds it.  Staged
