@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--spin-beta", type=float, default=0.0,
                     help="spin leg: inverse temperature of the OTOC curves (0: infinite temperature)")
     ap.add_argument("--serve-hbm-gb", type=float, default=150.0, help="served leg: device arena for live jobs")
+    ap.add_argument("--serve-capacity-requests", type=int, default=0,
+                    help="served leg: requests of the closed-loop capacity run (0: all of --serve-requests)")
     ap.add_argument("--serve-slots", type=int, default=256, help="served leg: jobs live at once")
     ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "sjf"],
                     help="served leg: admission order (fifo, or shortest estimated work first)")
@@ -414,8 +416,8 @@ def otoc_served(args, syk, torch):
     def workload(rate, seed):
         return [serve.Request(**r) for r in si.served_requests(n, rate=rate, seed=seed, **kw)]
 
-    # capacity: all requests present at t=0
-    cap_reqs = workload(1e9, 11)
+    # capacity: requests all present at t=0 (the first --serve-capacity-requests of them)
+    cap_reqs = workload(1e9, 11)[: args.serve_capacity_requests or n]
     srv = serve.OtocServer(dtype="c64", max_slots=args.serve_slots, hbm_budget_bytes=hbm, ticks_per_step=8,
                            policy=args.serve_policy)
     t0 = time.perf_counter()
@@ -432,6 +434,7 @@ def otoc_served(args, syk, torch):
     srv.close()
     summ = serve.summarize(res, wall)
     summ.update({"arrival_rate_per_s": rate, "closed_loop_capacity_per_s": cap, "load": args.serve_load,
+                 "capacity_requests": len(cap_reqs),
                  "workload": f"{n} Poisson requests, N 28..48 (P ~ 0.7^((N-28)/2)), k 0.5..4, beta 2..20, "
                              f"t 0..{args.serve_tmax:g} step {args.serve_dt:g}, c64, HBM budget "
                              f"{args.serve_hbm_gb:g} GiB, {args.serve_slots} slots, admission {args.serve_policy}"})

@@ -133,9 +133,19 @@ def work_estimate(r: Request, h) -> float:
     return float(nterms) * float(D) * float(len(t) + np.sum(np.abs(t)))
 
 
-def summarize(results, wall: float) -> dict:
+def summarize(results, wall: float, windows: int = 4) -> dict:
+    """Latency percentiles over all results and, to show whether the load is
+    sustained, over `windows` consecutive groups of requests in arrival order
+    (a queue that keeps growing shows as latencies rising window by window)."""
     lat = [r.latency for r in results]
+    by_arrival = sorted(results, key=lambda r: r.arrival)
+    win = []
+    if results and windows > 1:
+        for part in np.array_split(np.arange(len(by_arrival)), windows):
+            lw = [by_arrival[i].latency for i in part]
+            win.append({"arrivals_s": [by_arrival[part[0]].arrival, by_arrival[part[-1]].arrival],
+                        "p50_latency_s": percentile(lw, 50), "p99_latency_s": percentile(lw, 99)})
     return {"requests": len(results), "wall_s": wall, "realizations_per_s": len(results) / wall if wall > 0 else None,
             "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
             "mean_latency_s": float(np.mean(lat)) if lat else None,
-            "failed": sum(1 for r in results if r.status != 0)}
+            "failed": sum(1 for r in results if r.status != 0), "windows": win}
