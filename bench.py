@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--batch-states", type=int, default=4)
     ap.add_argument("--batch-slots", type=int, default=4096,
                     help="batch slots (jobs live at once; the rest wait for admission)")
+    ap.add_argument("--no-batch-autotune", action="store_true",
+                    help="batched leg: library default Krylov dimension and sync period, no autotuner")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-tmax", type=float, default=20.0)
     ap.add_argument("--serve-dt", type=float, default=1.0)
@@ -359,8 +361,20 @@ def otoc_batched(args, syk, si, torch, rank=0):
         q, J, _ = si.sample_sparse_syk(N, k, seed=700_000 + 1000 * rank + r)
         reals.append((N, q, J, syk.Terms(N, q, J, dtype="c64")))
     jobs = [(r, s) for r in range(R) for s in range(S)]
-    # Krylov dimension: the library default for complex64 (20; 30 measured 14% slower here)
-    b = syk.Batch(dtype="c64", max_slots=min(len(jobs), args.batch_slots), max_bytes=40 << 30)
+    # Krylov dimension and host sync period: picked by the library's batch
+    # autotuner on a random sample of these jobs (untimed, like plan building)
+    tune = None
+    m, tps = 0, 16
+    if not args.no_batch_autotune:
+        pick = rng.choice(len(jobs), size=min(len(jobs), 64), replace=False)
+        sample = [(reals[jobs[i][0]][3], reals[jobs[i][0]][0] - 1, reals[jobs[i][0]][0] - 2, beta, grid,
+                   1234 + jobs[i][0], jobs[i][1]) for i in pick]
+        t0 = time.perf_counter()
+        tune = syk.autotune_batch(sample, dtype="c64", max_bytes=8 << 30)
+        tune["tuning_s"] = time.perf_counter() - t0
+        tune["sample_jobs"] = len(sample)
+        m, tps = tune["m"], tune["ticks_per_sync"]
+    b = syk.Batch(dtype="c64", max_slots=min(len(jobs), args.batch_slots), max_bytes=40 << 30, m=m)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     results = {}
@@ -372,14 +386,15 @@ def otoc_batched(args, syk, si, torch, rank=0):
             if not b.submit(h, N - 1, N - 2, beta, grid, 1234 + r, s, tag):
                 break
             queue.pop(0)
-        for res in b.run(ticks_per_sync=16):
+        for res in b.run(ticks_per_sync=tps):
             results[res["tag"]] = res
     wall = time.perf_counter() - t0
     termamps = sum(results[t]["matvecs"] * reals[jobs[t][0]][3].n_terms * reals[jobs[t][0]][3].D for t in results)
     b.close()
     out = {"workload": f"{R} realisations x {S} states, N in 24..36, k in 1,2,4,8, beta=10, 11 t-points, c64",
            "realizations_per_s": R / wall, "curves_per_s": len(jobs) / wall, "wall_s": wall,
-           "matvec_Gtermamp_s": termamps / wall / 1e9, "failed": sum(1 for v in results.values() if v["status"])}
+           "matvec_Gtermamp_s": termamps / wall / 1e9, "failed": sum(1 for v in results.values() if v["status"]),
+           "krylov_m": m or "library default", "ticks_per_sync": tps, "autotune": tune}
     # plain FP64 single-realisation path (complex128, one realisation at a time)
     nplain = min(8, R)
     t0 = time.perf_counter()
@@ -405,7 +420,16 @@ def otoc_batched(args, syk, si, torch, rank=0):
 def otoc_served(args, syk, torch):
     """Served configuration (bounded): Poisson requests with N in 28..48
     weighted toward small N, k in {0.5,1,2,4}, beta in {2,5,10,20}; the arrival
-    rate is set to ~75% of the capacity measured by a closed-loop pass."""
+    rate is set to ~75% of the capacity measured by a closed-loop pass.
+
+    The mix is heavy-tailed (the work of a request grows like 2^(N/2) while its
+    weight falls like 0.7^(N/2)), so a few hundred requests can carry much less
+    or much more work per request than the served sample.  The closed-loop pass
+    therefore measures capacity in work units per second (serve.work_estimate:
+    terms x amplitudes x (grid points + sum |t|)), and the capacity in requests
+    per second of the served sample is that rate over the served sample's mean
+    work per request."""
+    import numpy as np
     from paper_2311_00639_b300 import serve
     import syk_inputs as si
 
@@ -413,31 +437,43 @@ def otoc_served(args, syk, torch):
     n = args.serve_requests
     hbm = int(args.serve_hbm_gb * (1 << 30))
 
-    def workload(rate, seed):
-        return [serve.Request(**r) for r in si.served_requests(n, rate=rate, seed=seed, **kw)]
+    def workload(count, seed):  # arrival times of a rate-1 Poisson process
+        return [serve.Request(**r) for r in si.served_requests(count, rate=1.0, seed=seed, **kw)]
 
-    # capacity: requests all present at t=0 (the first --serve-capacity-requests of them)
-    cap_reqs = workload(1e9, 11)[: args.serve_capacity_requests or n]
+    # capacity: requests all present at t=0 (a separate sample of the same mix)
+    cap_reqs = workload(args.serve_capacity_requests or n, 11)
+    for r in cap_reqs:
+        r.arrival = 0.0
     srv = serve.OtocServer(dtype="c64", max_slots=args.serve_slots, hbm_budget_bytes=hbm, ticks_per_step=8,
                            policy=args.serve_policy)
     t0 = time.perf_counter()
     res = srv.run(cap_reqs)
-    cap = len(res) / (time.perf_counter() - t0)
+    cap_wall = time.perf_counter() - t0
     srv.close()
-    rate = args.serve_load * cap
-    reqs = workload(rate, 12)
+    reqs = workload(n, 12)
+    rate, cap = serve.calibrated_rate(cap_reqs, cap_wall, reqs, args.serve_load)
+    cap_work = sum(serve.work_estimate(r, None) for r in cap_reqs) / cap_wall
+    mean_work = float(np.mean([serve.work_estimate(r, None) for r in reqs]))
+    for r in reqs:
+        r.arrival /= rate
     srv = serve.OtocServer(dtype="c64", max_slots=args.serve_slots, hbm_budget_bytes=hbm, ticks_per_step=8,
                            policy=args.serve_policy)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
     srv.close()
-    summ = serve.summarize(res, wall)
+    summ = serve.summarize(res, wall, work={r.rid: serve.work_estimate(r, None) for r in reqs},
+                           capacity_work_per_s=cap_work)
     summ.update({"arrival_rate_per_s": rate, "closed_loop_capacity_per_s": cap, "load": args.serve_load,
-                 "capacity_requests": len(cap_reqs),
+                 "capacity": {"requests": len(cap_reqs), "wall_s": cap_wall, "requests_per_s": len(cap_reqs) / cap_wall,
+                              "work_units_per_s": cap_work,
+                              "mean_work_per_request": sum(serve.work_estimate(r, None) for r in cap_reqs)
+                              / len(cap_reqs)},
+                 "served_mean_work_per_request": mean_work,
                  "workload": f"{n} Poisson requests, N 28..48 (P ~ 0.7^((N-28)/2)), k 0.5..4, beta 2..20, "
                              f"t 0..{args.serve_tmax:g} step {args.serve_dt:g}, c64, HBM budget "
-                             f"{args.serve_hbm_gb:g} GiB, {args.serve_slots} slots, admission {args.serve_policy}"})
+                             f"{args.serve_hbm_gb:g} GiB, {args.serve_slots} slots, admission {args.serve_policy}; "
+                             f"arrival rate = {args.serve_load:g} x closed-loop work rate / served mean work"})
     return summ
 
 
@@ -850,6 +886,29 @@ def ours(args):
         e2e = {"value": world * T * D / de / 1e9, "unit": UNIT, "h2d_bytes_per_step": D * 8,
                "d2h_bytes_per_step": D * 8, "ms_per_step": de * 1e3, "steps": ke,
                "pipeline": "3 streams, 2 device buffer sets: upload i+1 and download i overlap H psi i"}
+
+        # The host link alone: one step's upload, its download, and both at
+        # once on their two streams (the pipelined e2e step cannot beat the
+        # slower of the two-direction copy and the H psi).
+        def copies(h2d, d2h, reps=2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                if h2d:
+                    with torch.cuda.stream(s_in):
+                        din[0].copy_(hpsi, non_blocking=True)
+                if d2h:
+                    with torch.cuda.stream(s_out):
+                        hout.copy_(dout[1], non_blocking=True)
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) / reps
+
+        th, td, tb = copies(True, False), copies(False, True), copies(True, True)
+        bound = max(tb, per_step)
+        e2e["host_link"] = {"h2d_GBps": D * 8 / th / 1e9, "d2h_GBps": D * 8 / td / 1e9,
+                            "both_directions_ms": tb * 1e3, "step_bound_ms": bound * 1e3,
+                            "frac_of_bound": bound / de,
+                            "note": "bound = max(upload and download together, H psi); frac = bound / e2e step"}
         del hpsi, hout, din, dout
         torch.cuda.empty_cache()
 
@@ -951,7 +1010,7 @@ def ours(args):
         roof_l2 = {"bound": "l2", "achieved": staged / per_step / 1e12, "peak": stage_peak, "unit": "TB/s",
                    "frac": staged / per_step / 1e12 / stage_peak, "staged_bytes_per_step": staged,
                    "peak_source": "syk_probe_staging: 16 KiB bulk copies of a 32 MiB L2-resident buffer into "
-                                  "3 shared-memory stages, 4 CTAs per SM, consumers read each tile once; "
+                                  "the shared-memory stages and CTAs per SM of the store passes, consumers read each tile once; "
                                   "measured in this run",
                    "probe_TBps": {"staging_no_reads": stage_peak0, "staging_one_read": stage_peak,
                                   "plain_global_loads": ldg_peak},
@@ -959,6 +1018,22 @@ def ours(args):
                    "alu_frac_ceiling": t_alu / (staged / (stage_peak * 1e12))}
     except Exception as e:  # informational
         roof_l2 = {"error": str(e)[:200]}
+    # The second data path of the kernel: the consumers read every staged
+    # input once per term of its run (8 bytes per term x amplitude) and, in
+    # every pass after the first, the partial-sum tile once, with 16-byte
+    # shared-memory loads.  Peak: the same loads with nothing else running
+    # (syk_probe_smem), measured now.
+    try:
+        lds_peak = syk.probe_smem() / 1e12
+        lds = (T + h.info["n_passes"] - 1) * D * 8
+        roof_smem = {"bound": "smem", "achieved": lds / per_step / 1e12, "peak": lds_peak, "unit": "TB/s",
+                     "frac": lds / per_step / 1e12 / lds_peak, "lds_bytes_per_step": lds,
+                     "peak_source": "syk_probe_smem: 16-byte shared-memory loads, 8 CTAs of 128 threads per SM, "
+                                    "measured in this run",
+                     "time_bound_ms": lds / (lds_peak * 1e12) * 1e3,
+                     "alu_frac_ceiling": t_alu / (lds / (lds_peak * 1e12))}
+    except Exception as e:  # informational
+        roof_smem = {"error": str(e)[:200]}
 
     outlook = None
     if rank == 0 and not args.no_outlook:
@@ -990,6 +1065,7 @@ def ours(args):
                            "matvec_passes": h.info["n_passes"], "relabel": relabel_info},
                 "jw_identity_order": identity,
                 "gpu_launches": args.steps * h.info["n_passes"], "roofline": roof, "roofline_l2_staging": roof_l2,
+                "roofline_smem": roof_smem,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "fp64": fp64, "clocks": clk, "gpu": props.name, "otoc_batched": batched, "otoc_served": served,
                 "outlook_hpsi": outlook}

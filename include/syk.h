@@ -590,13 +590,14 @@ int syk_tridiag_exp(int m, const double* alpha, const double* beta, double z_re,
 
 /*
  * Hardware probes for the benchmark's roofline denominators (no paper
- * counterpart; the hot path never calls them).  Both synchronise `stream`.
+ * counterpart; the hot path never calls them).  Each synchronises `stream`.
  *
  * syk_probe_staging — bytes per second moved from `buf` (DEVICE, `bytes`
  * long, 16-byte aligned, at least 16 KiB; make it smaller than L2 to measure
- * L2 -> shared memory) by the complex64 matvec's pipeline shape: 16 KiB bulk
- * copies (cp.async.bulk + mbarrier), 3 stages, one producer lane and 4
- * consumer warps per CTA, 4 CTAs per SM, `jobs_per_cta` tiles per CTA on a
+ * L2 -> shared memory) by the pipeline shape of the complex64 matvec's store
+ * passes: 16 KiB bulk copies (cp.async.bulk + mbarrier), 2 stages, one
+ * producer lane and 4 consumer warps per CTA, 5 CTAs per SM, `jobs_per_cta`
+ * tiles per CTA on a
  * scattered walk over the buffer.  reads = 0: the consumers only wait for and
  * release each stage; 1 or 2: they also read every staged tile that many
  * times from shared memory (16-byte loads); -1: no shared memory, the same
@@ -607,6 +608,12 @@ int syk_tridiag_exp(int m, const double* alpha, const double* beta, double z_re,
  */
 int syk_probe_staging(const void* buf, size_t bytes, int reads, int jobs_per_cta, double* bytes_per_s,
                       syk_stream_t stream);
+/* syk_probe_smem — bytes per second of 16-byte shared-memory loads of the
+ * whole GPU (8 CTAs of 128 threads per SM, each streaming over a 16 KiB tile
+ * in its shared memory; a warp's load covers 512 contiguous bytes, as in the
+ * complex64 matvec consumers).  One warm-up launch, one timed launch (CUDA
+ * events).  Errors: SYK_EINVAL, SYK_ENOMEM, SYK_ECUDA. */
+int syk_probe_smem(double* bytes_per_s, syk_stream_t stream);
 /* syk_probe_fp64 — FP64 fused multiply-adds per second of the whole GPU
  * (8 independent chains per thread, 8 CTAs of 256 threads per SM). */
 int syk_probe_fp64(double* dfma_per_s, syk_stream_t stream);

@@ -94,6 +94,7 @@ SIGNATURES = {
     "syk_bounded_wait_selftest": (_I, [_P]),
     "syk_probe_staging": (_I, [_P, _SZ, _I, _I, C.POINTER(_D), _P]),
     "syk_probe_fp64": (_I, [C.POINTER(_D), _P]),
+    "syk_probe_smem": (_I, [C.POINTER(_D), _P]),
     "syk_relabel_majoranas": (_I, [_I, _I64, _P, _P, _I, _I64, _U64, _P, _P, _P, C.POINTER(_I64), C.POINTER(_I64)]),
     "syk_tridiag_exp": (_I, [_I, _P, _P, _D, _D, _D, _I, _P, C.POINTER(_D), C.POINTER(_D), C.POINTER(_I), _P]),
     "syk_last_error": (_I, [C.c_char_p, _SZ]),

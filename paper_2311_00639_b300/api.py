@@ -95,6 +95,13 @@ def tridiag_exp(alpha, beta, z: complex, tol: float, force_ql: bool = False, tim
     return out + (ms.value,) if timed else out
 
 
+def probe_smem(stream=None) -> float:
+    """Bytes per second of 16-byte shared-memory loads of the GPU (syk_probe_smem)."""
+    v = C.c_double(0.0)
+    L.check(L.load().syk_probe_smem(C.byref(v), _stream(stream)))
+    return v.value
+
+
 def probe_fp64(stream=None) -> float:
     """FP64 fused multiply-adds per second of the GPU (syk_probe_fp64)."""
     v = C.c_double(0.0)
@@ -639,6 +646,45 @@ class Batch:
         while self._pending:
             out += self.run(max_ticks, ticks_per_sync)
         return out
+
+
+def autotune_batch(jobs, dtype: str = "c64", ms=(16, 20, 24, 30), ticks=(8, 16, 32), max_slots: int = 0,
+                   max_bytes: int = 8 << 30, tol=None) -> dict:
+    """Pick the batched engine's Krylov dimension m and host sync period
+    (ticks between collections of finished jobs) by timing a sample of the
+    workload through syk_batch_*.
+
+    jobs: (terms, a, b, beta, t_grid, seed, state_id) tuples, e.g. a random
+    sample of the jobs of a batched run.  Each (m, ticks) pair runs the whole
+    sample in a fresh batch, after one untimed run; a pair with a failed job
+    is not chosen unless every pair has one.  Returns {"m", "ticks_per_sync",
+    "trials": [{"m", "ticks_per_sync", "s", "failed"}, ...]}."""
+    import time
+
+    torch = _torch()
+
+    def run(m, tps):
+        with Batch(dtype=dtype, max_slots=max_slots or len(jobs), max_bytes=max_bytes, m=m, tol=tol) as b:
+            queue = list(enumerate(jobs))
+            failed = 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while queue or b.pending:
+                while queue and b.submit(*queue[0][1], tag=queue[0][0]):
+                    queue.pop(0)
+                for res in b.run(ticks_per_sync=tps):
+                    failed += int(res["status"] != 0)
+            return time.perf_counter() - t0, failed
+
+    run(ms[0], ticks[0])  # first use: graph capture, module loading
+    trials = []
+    for m in ms:
+        for tps in ticks:
+            wall, failed = run(m, tps)
+            trials.append({"m": int(m), "ticks_per_sync": int(tps), "s": wall, "failed": failed})
+    ok = [t for t in trials if t["failed"] == 0] or trials
+    best = min(ok, key=lambda t: t["s"])
+    return {"m": best["m"], "ticks_per_sync": best["ticks_per_sync"], "trials": trials}
 
 
 def exact_trace_otoc(terms: "Terms", pairs, beta: float, t_grid, max_slots: int = 4096, max_bytes: int = 8 << 30,

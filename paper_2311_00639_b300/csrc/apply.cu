@@ -372,7 +372,8 @@ __global__ void __launch_bounds__(256) k_matvec_tma(MV<Real> p, int* err_flag) {
 // (p.prev).  k_sum_chunks then adds the chunks in order, so the result does not
 // depend on which CTA ran which chunk.
 template <int EPI, bool ACCUM, int S, bool SPLIT = false>
-__global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_matvec_c64(MV<float> p, int* err_flag) {
+__global__ void __launch_bounds__(32 * (kConsumerWarps + 1), EPI == EPI_STORE ? kC64CtasPerSm : kC64EpiCtasPerSm)
+    k_matvec_c64(MV<float> p, int* err_flag) {
   static_assert(!SPLIT || EPI == EPI_STORE, "split passes only store their sum");
   constexpr uint32_t kTileBytes = (1u << kTileBits) * 8u;
   constexpr bool kQueue = EPI == EPI_STORE;
@@ -938,8 +939,9 @@ Shape shape_of(const syk_terms* h) {
   if (D >= (1ull << kTileBits) && !c128_gather) {
     s.R = 8;
     s.warps = 8;
-    // CTAs resident per SM given the stage buffers.
-    const uint64_t per_sm = h->dtype == SYK_C128 ? 2 : static_cast<uint64_t>(kC64CtasPerSm);
+    // CTAs resident per SM given the stage buffers (complex64: the shape of the
+    // passes with a Lanczos epilogue, the only ones launched on this grid)
+    const uint64_t per_sm = h->dtype == SYK_C128 ? 2 : static_cast<uint64_t>(kC64EpiCtasPerSm);
     s.grid = static_cast<int>(std::min<uint64_t>(D >> kTileBits, ntiles_cap * per_sm));
     return s;
   }
@@ -954,12 +956,13 @@ template <typename Real, int EPI, bool ACCUM>
 void launch_pass(const syk_terms* h, const Shape& s, const MV<Real>& q, unsigned gy, cudaStream_t st) {
   if constexpr (std::is_same<Real, float>::value) {
     if (s.R == 8) {
-      constexpr size_t dyn = static_cast<size_t>(kStagesC64) * (1u << kTileBits) * 8u;
+      constexpr int S = EPI == EPI_STORE ? kStagesC64 : kStagesC64Epi;
+      constexpr size_t dyn = static_cast<size_t>(S) * (1u << kTileBits) * 8u;
       static std::atomic<uint64_t> configured{0};
       const uint64_t bit = 1ull << (h->device & 63);
       if (!(configured.load() & bit)) {
-        SYK_CUDA(cudaFuncSetAttribute(k_matvec_c64<EPI, ACCUM, kStagesC64>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn)));
+        SYK_CUDA(cudaFuncSetAttribute(k_matvec_c64<EPI, ACCUM, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(dyn)));
         configured.fetch_or(bit);
       }
       if (EPI == EPI_STORE) {  // one-dimensional over (state, tile) items taken from the handle's counter
@@ -968,9 +971,9 @@ void launch_pass(const syk_terms* h, const Shape& s, const MV<Real>& q, unsigned
         qq.ny = gy;
         const uint64_t items = (static_cast<uint64_t>(h->D) >> kTileBits) * gy;
         const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(items, static_cast<uint64_t>(h->n_sm) * kC64CtasPerSm));
-        k_matvec_c64<EPI, ACCUM, kStagesC64><<<grid, 32 * (kConsumerWarps + 1), dyn, st>>>(qq, h->d_err);
+        k_matvec_c64<EPI, ACCUM, S><<<grid, 32 * (kConsumerWarps + 1), dyn, st>>>(qq, h->d_err);
       } else {
-        k_matvec_c64<EPI, ACCUM, kStagesC64><<<dim3(s.grid, gy), 32 * (kConsumerWarps + 1), dyn, st>>>(q, h->d_err);
+        k_matvec_c64<EPI, ACCUM, S><<<dim3(s.grid, gy), 32 * (kConsumerWarps + 1), dyn, st>>>(q, h->d_err);
       }
       return;
     }

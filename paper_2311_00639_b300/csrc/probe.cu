@@ -1,11 +1,14 @@
 // Hardware probes for the roofline denominators the benchmark reports (the
 // paper has no counterpart; nothing on the hot path calls them):
 //   * syk_probe_staging — the rate at which 16 KiB bulk copies (cp.async.bulk
-//     + mbarrier, 3 stages, one producer lane and 4 consumer warps per CTA,
-//     4 CTAs per SM: the complex64 matvec's pipeline) move an L2-resident
+//     + mbarrier, one producer lane and 4 consumer warps per CTA, the stages
+//     and CTAs per SM of the complex64 matvec's store passes) move an L2-resident
 //     buffer into shared memory, with the consumers reading every staged tile
 //     0, 1 or 2 times; or, for comparison, the rate of plain 16-byte global
 //     loads of the same tiles (no shared memory);
+//   * syk_probe_smem — the rate of 16-byte shared-memory loads of the whole GPU
+//     in the complex64 matvec consumers' pattern (a warp reads 512 contiguous
+//     bytes per load, no bank conflicts), with nothing else running;
 //   * syk_probe_fp64 — the FP64 fused multiply-add rate of the whole GPU
 //     (independent chains, all SMs).
 // Every wait is bounded as in the matvec pipelines.
@@ -20,9 +23,17 @@ namespace syk {
 namespace {
 
 constexpr uint32_t kProbeTileBytes = 16384;
-constexpr int kProbeStages = 3;
+constexpr int kProbeStages = kStagesC64;
 constexpr int kProbeConsumers = 4;
-constexpr int kProbeCtasPerSm = 4;
+constexpr int kProbeCtasPerSm = kC64CtasPerSm;
+
+// One 16-byte shared-memory load that the compiler may not merge with another
+// load of the same address (a probe reads the same tile more than once).
+__device__ __forceinline__ float4 lds128_volatile(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
 
 // Tile visited by job q of CTA b: a scattered walk over the buffer's tiles.
 __device__ __forceinline__ uint32_t probe_tile(uint32_t b, uint32_t q, uint32_t ntiles) {
@@ -30,7 +41,7 @@ __device__ __forceinline__ uint32_t probe_tile(uint32_t b, uint32_t q, uint32_t 
 }
 
 template <int READS>
-__global__ void __launch_bounds__(32 * (kProbeConsumers + 1)) k_probe_stage(const float4* __restrict__ buf,
+__global__ void __launch_bounds__(32 * (kProbeConsumers + 1), kProbeCtasPerSm) k_probe_stage(const float4* __restrict__ buf,
                                                                               uint32_t ntiles, uint32_t jobs,
                                                                               int* err, float* sink) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -77,12 +88,12 @@ __global__ void __launch_bounds__(32 * (kProbeConsumers + 1)) k_probe_stage(cons
     for (uint32_t q = 0; q < jobs; ++q) {
       const uint32_t stg = q % kProbeStages;
       if (!mbar_wait_bounded(smem_u32(&full_bar[stg]), (q / kProbeStages) & 1u, &s_err)) break;
-      const float4* t4 = reinterpret_cast<const float4*>(smem_raw + stg * kProbeTileBytes);
+      const uint32_t t4 = smem_u32(smem_raw + stg * kProbeTileBytes);
 #pragma unroll
       for (int r = 0; r < READS; ++r)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {  // 1024 float4 per tile: 8 per consumer thread
-          const float4 v = t4[(warp * 32u + lane) + 128u * i];
+          const float4 v = lds128_volatile(t4 + 16u * ((warp * 32u + lane) + 128u * i));
           acc += (v.x + v.y) + (v.z + v.w);
         }
       __syncwarp();
@@ -110,6 +121,30 @@ __global__ void __launch_bounds__(128) k_probe_ldg(const float4* __restrict__ bu
     }
   }
   if (acc == 1234.5f) *sink = acc;
+}
+
+// Shared-memory loads only: each thread of a 128-thread CTA reads 8 float4 of
+// a 16 KiB tile per iteration (index (thread + 128 i + 32 it) mod 1024, so a
+// warp's load covers 512 contiguous bytes), into four independent sums.
+constexpr int kLdsThreads = 128;
+constexpr int kLdsCtasPerSm = 8;
+__global__ void __launch_bounds__(kLdsThreads) k_probe_lds(int iters, float* sink) {
+  extern __shared__ __align__(16) float4 tile[];  // 1024 float4
+  for (uint32_t i = threadIdx.x; i < 1024u; i += kLdsThreads) tile[i] = make_float4(1e-7f * i, 1.f, 2.f, 3.f);
+  __syncthreads();
+  const uint32_t base = smem_u32(tile);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  for (uint32_t it = 0; it < static_cast<uint32_t>(iters); ++it) {
+#pragma unroll
+    for (uint32_t i = 0; i < 8u; ++i) {
+      const float4 v = lds128_volatile(base + 16u * ((threadIdx.x + 128u * i + 32u * it) & 1023u));
+      s0 += v.x;
+      s1 += v.y;
+      s2 += v.z;
+      s3 += v.w;
+    }
+  }
+  if ((s0 + s1) + (s2 + s3) == 1234.5f) *sink = s0;  // keeps the loads
 }
 
 __global__ void __launch_bounds__(256) k_probe_dfma(double* sink, int iters) {
@@ -215,6 +250,28 @@ extern "C" int syk_probe_staging(const void* buf, size_t bytes, int reads, int j
     SYK_CUDA(cudaMemcpy(&e, pb.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) throw syk::Error(SYK_ETIMEOUT, "a bounded wait expired");
     *bytes_per_s = static_cast<double>(grid) * jobs_per_cta * syk::kProbeTileBytes / (ms * 1e-3);
+  });
+}
+
+extern "C" int syk_probe_smem(double* bytes_per_s, syk_stream_t stream) {
+  return syk::probe_guard("syk_probe_smem", [&] {
+    SYK_REQUIRE(bytes_per_s, "null argument");
+    auto st = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, nsm = 0;
+    SYK_CUDA(cudaGetDevice(&dev));
+    SYK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    syk::ProbeBuffers pb;
+    const int grid = nsm * syk::kLdsCtasPerSm, iters = 4096;
+    const size_t dyn = 16384;
+    syk::k_probe_lds<<<grid, syk::kLdsThreads, dyn, st>>>(64, pb.sink);  // warm-up
+    SYK_CUDA(cudaGetLastError());
+    SYK_CUDA(cudaEventRecord(pb.e0, st));
+    syk::k_probe_lds<<<grid, syk::kLdsThreads, dyn, st>>>(iters, pb.sink);
+    SYK_CUDA(cudaEventRecord(pb.e1, st));
+    SYK_CUDA(cudaEventSynchronize(pb.e1));
+    float ms = 0.f;
+    SYK_CUDA(cudaEventElapsedTime(&ms, pb.e0, pb.e1));
+    *bytes_per_s = static_cast<double>(grid) * syk::kLdsThreads * 8.0 * 16.0 * iters / (ms * 1e-3);
   });
 }
 

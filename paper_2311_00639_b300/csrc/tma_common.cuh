@@ -106,20 +106,28 @@ constexpr int kRows = SYK_C64_ROWS;
 constexpr int kConsumerWarps = (1 << kTileBits) / (64 * kRows);
 constexpr uint32_t kRowMask = static_cast<uint32_t>(kRows - 1) << 6;  // amplitude bits chosen by the row
 constexpr uint32_t kPairXMask = 0x7FEu & ~kRowMask;                    // in-tile flip bits applied per lane
-// 3 stages x 4 CTAs per SM (96 registers a thread) beat 4 x 3 on B300: the
-// extra consumer warps hide more of the bulk-copy latency for the same bytes
-// in flight per SM.
+// Pipeline shape of the passes that only store their sum (the H psi passes
+// and every pass but the last of a Lanczos matvec): 2 stages x 5 CTAs per SM
+// (72 registers a thread).  The consumers, not the staging depth, bound these
+// passes, so more consumer warps per SM beat deeper staging.  Measured on B300,
+// N=64 H psi: 2 x 5 180.6 ms, 3 x 4 185.8, 2 x 4 192.8, 3 x 3 217.9;
+// N=56: 8.85 / 9.25 ms for 2 x 5 / 3 x 4.
 #ifndef SYK_C64_STAGES
-#define SYK_C64_STAGES 3
+#define SYK_C64_STAGES 2
 #endif
 constexpr int kStagesC64 = SYK_C64_STAGES;
 #ifndef SYK_C64_MAX_CTAS
-#define SYK_C64_MAX_CTAS 4
+#define SYK_C64_MAX_CTAS 5
 #endif
 // CTAs per SM: shared memory holds S 16 KiB stages each (<= 227 KiB per SM),
 // at most SYK_C64_MAX_CTAS (the register budget of __launch_bounds__).
 constexpr int kC64CtasPerSm = (227 / (16 * kStagesC64 + 2)) < SYK_C64_MAX_CTAS ? (227 / (16 * kStagesC64 + 2))
                                                                                : SYK_C64_MAX_CTAS;
+// Passes with a Lanczos epilogue (EPI_LANCZOS, EPI_RECUR) hold the epilogue's
+// operands beside the row sums: 3 stages x 4 CTAs per SM, 96 registers a
+// thread (at 72 their epilogues spill).
+constexpr int kStagesC64Epi = 3;
+constexpr int kC64EpiCtasPerSm = 4;
 
 template <bool IMAG, bool XS, bool ZS, int XR>
 __device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t pa2, const float (&c)[kRows],

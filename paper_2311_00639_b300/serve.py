@@ -133,18 +133,49 @@ def work_estimate(r: Request, h) -> float:
     return float(nterms) * float(D) * float(len(t) + np.sum(np.abs(t)))
 
 
-def summarize(results, wall: float, windows: int = 4) -> dict:
+def calibrated_rate(capacity_requests, capacity_wall_s: float, served, load: float) -> tuple:
+    """Poisson arrival rate that offers `load` (e.g. 0.75) of the server's
+    capacity for the requests in `served`.
+
+    The capacity is measured by a closed-loop pass over `capacity_requests`
+    (all present at t = 0, finished in capacity_wall_s); it is taken in work
+    units per second (work_estimate) and converted to requests per second of
+    the served sample through the served sample's own mean work, so that a
+    capacity sample lighter or heavier than the served one (a heavy-tailed
+    size mix) does not over- or under-load the server.  Returns
+    (rate, capacity in requests per second of the served sample)."""
+    if capacity_wall_s <= 0 or not capacity_requests or not served:
+        raise ValueError("need a positive wall time and non-empty samples")
+    cap_work = sum(work_estimate(r, None) for r in capacity_requests) / capacity_wall_s
+    mean_work = float(np.mean([work_estimate(r, None) for r in served]))
+    cap = cap_work / mean_work
+    return load * cap, cap
+
+
+def summarize(results, wall: float, windows: int = 4, work=None, capacity_work_per_s=None) -> dict:
     """Latency percentiles over all results and, to show whether the load is
     sustained, over `windows` consecutive groups of requests in arrival order
-    (a queue that keeps growing shows as latencies rising window by window)."""
+    (a queue that keeps growing shows as latencies rising window by window).
+    With work (rid -> work_estimate) and the closed-loop capacity in work units
+    per second, each window also reports its offered load: the work that
+    arrived in it over its arrival span, as a fraction of the capacity (a
+    heavy-tailed mix offers some windows much more than the average)."""
     lat = [r.latency for r in results]
     by_arrival = sorted(results, key=lambda r: r.arrival)
     win = []
     if results and windows > 1:
-        for part in np.array_split(np.arange(len(by_arrival)), windows):
+        parts = np.array_split(np.arange(len(by_arrival)), windows)
+        for k, part in enumerate(parts):
             lw = [by_arrival[i].latency for i in part]
-            win.append({"arrivals_s": [by_arrival[part[0]].arrival, by_arrival[part[-1]].arrival],
-                        "p50_latency_s": percentile(lw, 50), "p99_latency_s": percentile(lw, 99)})
+            w = {"arrivals_s": [by_arrival[part[0]].arrival, by_arrival[part[-1]].arrival],
+                 "p50_latency_s": percentile(lw, 50), "p99_latency_s": percentile(lw, 99)}
+            if work is not None and capacity_work_per_s:
+                # span from the window's first arrival to the next window's first
+                end = by_arrival[parts[k + 1][0]].arrival if k + 1 < len(parts) else by_arrival[part[-1]].arrival
+                span = end - by_arrival[part[0]].arrival
+                if span > 0:
+                    w["offered_load"] = sum(work[by_arrival[i].rid] for i in part) / span / capacity_work_per_s
+            win.append(w)
     return {"requests": len(results), "wall_s": wall, "realizations_per_s": len(results) / wall if wall > 0 else None,
             "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
             "mean_latency_s": float(np.mean(lat)) if lat else None,

@@ -139,3 +139,29 @@ def test_batch_green_function_matches_oracle(syk, dtype):
             pU, pD = philox_normed(N, 17, tag)
             ref = ot.G_state_blocks(N, rep, HU, HD, X, a, beta, ts, pU, pD)
             assert np.max(np.abs(res[tag]["F"] - ref)) < tol
+
+
+def test_autotune_batch_picks_a_clean_setting(syk):
+    """The batch autotuner times every (m, sync period) pair on the sample,
+    returns one of them, and the chosen m reproduces the default-m curves
+    within the complex64 Krylov tolerance."""
+    ts = np.array([0.0, 1.0, 2.0, 4.0])
+    hs = [syk.Terms(N, *si.sample_sparse_syk(N, 4, r=30 + N)[:2], dtype="c64") for N in (12, 16, 24)]
+    try:
+        sample = [(h, h.N - 1, h.N - 2, 2.0, ts, 5, s) for h in hs for s in range(2)]
+        tune = syk.autotune_batch(sample, ms=(12, 20), ticks=(4, 8), max_bytes=64 << 20)
+        assert len(tune["trials"]) == 4
+        assert all(t["failed"] == 0 and t["s"] > 0 for t in tune["trials"])
+        assert (tune["m"], tune["ticks_per_sync"]) in {(t["m"], t["ticks_per_sync"]) for t in tune["trials"]}
+        curves = {}
+        for m in (0, tune["m"]):
+            with syk.Batch(dtype="c64", max_slots=8, max_bytes=64 << 20, m=m) as b:
+                for tag, job in enumerate(sample):
+                    assert b.submit(*job, tag=tag)
+                curves[m] = {r["tag"]: r["F"] for r in b.drain()}
+        for tag in range(len(sample)):
+            ref = curves[0][tag]
+            assert np.max(np.abs(curves[tune["m"]][tag] - ref)) / np.max(np.abs(ref)) < 2e-5
+    finally:
+        for h in hs:
+            h.close()

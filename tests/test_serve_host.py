@@ -119,3 +119,39 @@ def test_served_workload_distribution():
     assert np.allclose(reqs[0]["t_grid"], [0.0, 0.5, 1.0])
     arr = np.array([r["arrival"] for r in reqs])
     assert np.allclose(arr, serve.poisson_arrivals(300, rate=10.0, seed=2))
+
+
+def _req(rid, N, n_terms, t_max, dt=1.0):
+    return serve.Request(rid=rid, arrival=0.0, N=N, quads=np.zeros((n_terms, 4), np.int32), J=np.ones(n_terms),
+                         beta=1.0, t_grid=np.arange(0.0, t_max + 1e-9, dt), seed=0)
+
+
+def test_calibrated_rate_uses_work_not_request_counts():
+    """A capacity sample lighter than the served one must lower the rate in
+    proportion to the served sample's mean work (the heavy-tailed mix)."""
+    light = [_req(i, 28, 100, 2.0) for i in range(10)]
+    heavy = [_req(i, 28, 100, 2.0) for i in range(9)] + [_req(9, 36, 100, 2.0)]  # one request 16x heavier
+    w = serve.work_estimate(light[0], None)
+    assert w == 100 * 2 ** 13 * (3 + 3.0)  # terms x D x (grid points + sum |t|)
+    rate_same, cap_same = serve.calibrated_rate(light, 2.0, light, 0.75)
+    assert abs(cap_same - 5.0) < 1e-12 and abs(rate_same - 3.75) < 1e-12  # 10 requests in 2 s
+    rate, cap = serve.calibrated_rate(light, 2.0, heavy, 0.75)
+    assert abs(cap - 5.0 * 10 / (9 + 16)) < 1e-12
+    assert abs(rate - 0.75 * cap) < 1e-12
+    try:
+        serve.calibrated_rate(light, 0.0, heavy, 0.75)
+        assert False, "zero wall time accepted"
+    except ValueError:
+        pass
+
+
+def test_summarize_windows_report_offered_load():
+    res = [serve.Result(rid=i, N=28, F=None, otoc=None, arrival=float(i), admitted=float(i), done=float(i) + 1.0,
+                        matvecs=1, status=0) for i in range(8)]
+    work = {i: (3.0 if i >= 4 else 1.0) for i in range(8)}
+    s = serve.summarize(res, 9.0, windows=2, work=work, capacity_work_per_s=2.0)
+    w0, w1 = s["windows"]
+    assert abs(w0["offered_load"] - 4 * 1.0 / 4.0 / 2.0) < 1e-12  # 4 units over arrivals 0..4
+    assert abs(w1["offered_load"] - 4 * 3.0 / 3.0 / 2.0) < 1e-12  # last window: span 4..7
+    assert w0["p50_latency_s"] == 1.0 and s["requests"] == 8
+    assert "offered_load" not in serve.summarize(res, 9.0, windows=2)["windows"][0]
