@@ -71,6 +71,10 @@ def parse():
     ap.add_argument("--batch-states", type=int, default=4)
     ap.add_argument("--batch-slots", type=int, default=4096,
                     help="batch slots (jobs live at once; the rest wait for admission)")
+    ap.add_argument("--batch-N", type=int, default=0, help="batched leg: fixed N for every realisation (0: 24..36)")
+    ap.add_argument("--batch-k", type=float, default=3.0, help="batched leg: k with --batch-N")
+    ap.add_argument("--batch-no-plain", action="store_true",
+                    help="batched leg: skip the plain FP64 single-realisation comparison")
     ap.add_argument("--no-batch-autotune", action="store_true",
                     help="batched leg: library default Krylov dimension and sync period, no autotuner")
     ap.add_argument("--serve-requests", type=int, default=48)
@@ -358,6 +362,8 @@ def otoc_batched(args, syk, si, torch, rank=0):
     for r in range(R):
         N = int(rng.choice(np.arange(24, 37, 2)))
         k = float(rng.choice([1.0, 2.0, 4.0, 8.0]))
+        if args.batch_N:  # one size for every realisation (e.g. a paper row through the batched engine)
+            N, k = args.batch_N, args.batch_k
         q, J, _ = si.sample_sparse_syk(N, k, seed=700_000 + 1000 * rank + r)
         reals.append((N, q, J, syk.Terms(N, q, J, dtype="c64")))
     jobs = [(r, s) for r in range(R) for s in range(S)]
@@ -391,12 +397,13 @@ def otoc_batched(args, syk, si, torch, rank=0):
     wall = time.perf_counter() - t0
     termamps = sum(results[t]["matvecs"] * reals[jobs[t][0]][3].n_terms * reals[jobs[t][0]][3].D for t in results)
     b.close()
-    out = {"workload": f"{R} realisations x {S} states, N in 24..36, k in 1,2,4,8, beta=10, 11 t-points, c64",
+    sizes = f"N={args.batch_N}, k={args.batch_k:g}" if args.batch_N else "N in 24..36, k in 1,2,4,8"
+    out = {"workload": f"{R} realisations x {S} states, {sizes}, beta=10, 11 t-points, c64",
            "realizations_per_s": R / wall, "curves_per_s": len(jobs) / wall, "wall_s": wall,
            "matvec_Gtermamp_s": termamps / wall / 1e9, "failed": sum(1 for v in results.values() if v["status"]),
            "krylov_m": m or "library default", "ticks_per_sync": tps, "autotune": tune}
     # plain FP64 single-realisation path (complex128, one realisation at a time)
-    nplain = min(8, R)
+    nplain = 0 if args.batch_no_plain else min(8, R)
     t0 = time.perf_counter()
     diffs = []
     for r in range(nplain):
@@ -409,8 +416,9 @@ def otoc_batched(args, syk, si, torch, rank=0):
                 F64, _, _ = h64.otoc(N - 1, N - 2, beta, grid, psi=psi)
                 diffs.append(np.max(np.abs(results[r * S + s]["F"] - F64[0])) / np.max(np.abs(F64[0])))
     plain_wall = time.perf_counter() - t0
-    out["plain_fp64_single_path"] = {"realizations_per_s": nplain / plain_wall, "realizations": nplain,
-                                     "note": "syk_otoc complex128, one realisation and state at a time"}
+    if nplain:
+        out["plain_fp64_single_path"] = {"realizations_per_s": nplain / plain_wall, "realizations": nplain,
+                                         "note": "syk_otoc complex128, one realisation and state at a time"}
     out["c64_vs_fp64_max_rel_F_diff"] = float(max(diffs)) if diffs else None
     for r in reals:
         r[3].close()
