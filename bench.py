@@ -50,6 +50,7 @@ def parse():
                          "nonherm: non-Hermitian SYK, H psi and Arnoldi OTOC curves; paper-rows: time per OTOC "
                          "curve of the paper's benchmark rows; config2: the N=32 mixed-precision error statement)")
     ap.add_argument("--rows-N", default="30,38,46", help="paper-rows: the N values (k=3, beta=0.05)")
+    ap.add_argument("--rows-dense-N", default="30", help="paper-rows: N values of dense SYK rows ('' for none)")
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--k", type=float, default=4.0)
     ap.add_argument("--no-fp64", action="store_true")
@@ -494,9 +495,11 @@ def paper_rows(args, syk, si, torch):
 
     grid = np.linspace(0.0, 10.0, 11)
     rows = []
-    for N in [int(v) for v in args.rows_N.split(",")]:
-        q, J, _ = si.sample_sparse_syk(N, 3.0, r=0)
-        row = {"N": N, "k": 3, "beta": 0.05, "terms": len(J)}
+    sizes = [(int(v), 3.0) for v in args.rows_N.split(",") if v]
+    sizes += [(int(v), "dense") for v in args.rows_dense_N.split(",") if v]
+    for N, k in sizes:
+        q, J, _ = si.sample_dense_syk(N, seed=0) if k == "dense" else si.sample_sparse_syk(N, k, r=0)
+        row = {"N": N, "k": k if k == "dense" else 3, "beta": 0.05, "terms": len(J)}
         for dtype in ("c128", "c64"):
             with syk.Terms(N, q, J, dtype=dtype) as h:
                 h.otoc(N - 1, N - 2, 0.05, grid[:2], n_states=1, seed=9)  # warm-up (captures the Krylov loops)
@@ -507,8 +510,11 @@ def paper_rows(args, syk, si, torch):
                 row[f"{dtype}_matvecs"] = st.matvecs
                 row[f"{dtype}_substeps"] = st.substeps
                 row[f"{dtype}_otoc_t10"] = float(o[-1])
+                if dtype == "c64":
+                    row["c64_merged_terms"] = h.info["n_merged"]
         rows.append(row)
-    return {"workload": "paper benchmark rows, sparse k=3, beta=0.05, one Philox state, 11 t-points",
+    return {"workload": "paper benchmark rows, sparse k=3 (and dense SYK with --rows-dense-N), beta=0.05, "
+                        "one Philox state, 11 t-points",
             "rows": rows}
 
 

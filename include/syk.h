@@ -81,6 +81,8 @@ typedef struct {
   int64_t n_tile_reads; /* input tiles staged per output tile over all passes of one H psi:
                            complex64 terms of a pass that read the same tile share one copy;
                            complex128 stages one tile per term */
+  int64_t n_merged;     /* complex64: terms whose body runs with the next term's (same flip mask and
+                           class: one body per group of such terms); 0 for complex128 */
 } syk_terms_info;
 
 /*
@@ -162,7 +164,8 @@ typedef struct {
   uint32_t* records;  /* [2][n_terms + 1][4]: the complex64 records of block U, then D, as the
                          kernel reads them: x, z, coefficient (float bits), flags */
   int64_t n_terms, n_passes;
-  int64_t n_runs; /* records that start a run (a new staged input tile) */
+  int64_t n_runs;   /* records that start a run (a new staged input tile) */
+  int64_t n_merges; /* records flagged "merge with the next" (flags bit 4) */
 } syk_plan_host_out;
 
 /*
@@ -171,7 +174,9 @@ typedef struct {
  * straggler_ratio) sets up for these terms, on a device with n_sm SMs.
  * Same argument rules as syk_build_terms and syk_terms_replan.  Records
  * within a pass are ordered by (x >> 11, class, x, z); flags bit 0
- * straggler, 1 run start, 2 run end, 3 imaginary coefficient, bits 8-13 the
+ * straggler, 1 run start, 2 run end, 3 imaginary coefficient, 4 merge (the
+ * next record of the pass has the same x and class: the kernel sums the two
+ * terms' coefficients and applies their shared body once), bits 8-13 the
  * consumer body 32 imag + 16 (x & 1) + 8 (z & 1) + ((x >> 6) & 7); bit 31 of
  * flags, x and z hold bits 6, 7 and 8 of z (x and z fit in 31 bits).
  * Errors: SYK_EINVAL.

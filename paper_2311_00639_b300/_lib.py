@@ -17,7 +17,7 @@ class TermsInfo(C.Structure):
     _fields_ = [("N", C.c_int), ("L", C.c_int), ("dtype", C.c_int), ("rep", C.c_int), ("D", C.c_int64),
                 ("n_input", C.c_int64), ("n_terms", C.c_int64), ("n_real", C.c_int64),
                 ("n_xgroups", C.c_int64), ("sum_abs_coef", C.c_double), ("n_passes", C.c_int64),
-                ("device_error", C.c_int64), ("n_tile_reads", C.c_int64)]
+                ("device_error", C.c_int64), ("n_tile_reads", C.c_int64), ("n_merged", C.c_int64)]
 
 
 class KrylovParams(C.Structure):
@@ -46,7 +46,7 @@ class PlanHostOut(C.Structure):
     _fields_ = [("term_capacity", C.c_int64), ("pass_capacity", C.c_int64), ("passes", C.c_void_p),
                 ("x", C.c_void_p), ("z", C.c_void_p), ("coef_U", C.c_void_p), ("coef_D", C.c_void_p),
                 ("imag", C.c_void_p), ("straggler", C.c_void_p), ("records", C.c_void_p),
-                ("n_terms", C.c_int64), ("n_passes", C.c_int64), ("n_runs", C.c_int64)]
+                ("n_terms", C.c_int64), ("n_passes", C.c_int64), ("n_runs", C.c_int64), ("n_merges", C.c_int64)]
 
 
 # name -> (restype, argtypes); every symbol include/syk.h declares.

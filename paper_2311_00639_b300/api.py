@@ -138,6 +138,7 @@ def _plan_outputs(call) -> dict:
                       **{k: v.ctypes.data for k, v in out.items()})
     L.check(call(C.byref(o)))
     out["n_runs"] = o.n_runs
+    out["n_merges"] = o.n_merges
     out["passes"] = [{"t0": p.t0, "ti": p.ti, "t1": p.t1, "emask": p.emask, "cls": list(p.cls),
                       "split_chunks": p.split_chunks, "split_terms": p.split_terms,
                       "dep": np.array([list(p.dep[b]) for b in range(3)], np.uint32)} for p in passes[:P]]

@@ -371,8 +371,8 @@ __global__ void __launch_bounds__(256) k_matvec_tma(MV<Real> p, int* err_flag) {
 // to p.out + c D (a workspace); chunk 0 also carries the earlier passes' sum
 // (p.prev).  k_sum_chunks then adds the chunks in order, so the result does not
 // depend on which CTA ran which chunk.
-template <int EPI, bool ACCUM, int S, bool SPLIT = false>
-__global__ void __launch_bounds__(32 * (kConsumerWarps + 1), EPI == EPI_STORE ? kC64CtasPerSm : kC64EpiCtasPerSm)
+template <int EPI, bool ACCUM, int S, bool SPLIT = false, bool MERGE = false>
+__global__ void __launch_bounds__(32 * (kConsumerWarps + 1), c64_ctas_for_stages(S))
     k_matvec_c64(MV<float> p, int* err_flag) {
   static_assert(!SPLIT || EPI == EPI_STORE, "split passes only store their sum");
   constexpr uint32_t kTileBytes = (1u << kTileBits) * 8u;
@@ -536,7 +536,8 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), EPI == EPI_STORE ? 
 #pragma unroll
         for (int r = 0; r < kRows; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
       }
-      c64_terms<S, SPLIT>(ct0, ct1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err, lane);
+      c64_terms<S, SPLIT, MERGE>(ct0, ct1, d, ring, a, p.rec, mt, pair_part, smem_raw, full_bar, empty_bar, &s_err,
+                                 lane);
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
         const uint32_t i4 = (mt >> 1) + 32u * r;
@@ -952,28 +953,44 @@ Shape shape_of(const syk_terms* h) {
   return s;
 }
 
+// One complex64 pass on the TMA-staged kernel of the handle's shape.
+template <int EPI, bool ACCUM, bool MERGE, int S>
+void launch_c64_pass(const syk_terms* h, const Shape& s, const MV<float>& q, unsigned gy, cudaStream_t st) {
+  constexpr size_t dyn = static_cast<size_t>(S) * (1u << kTileBits) * 8u;
+  static std::atomic<uint64_t> configured{0};
+  const uint64_t bit = 1ull << (h->device & 63);
+  if (!(configured.load() & bit)) {
+    SYK_CUDA(cudaFuncSetAttribute(k_matvec_c64<EPI, ACCUM, S, false, MERGE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn)));
+    configured.fetch_or(bit);
+  }
+  if (EPI == EPI_STORE) {  // one-dimensional over (state, tile) items taken from the handle's counter
+    MV<float> qq = q;
+    qq.sched = h->d_sched;
+    qq.ny = gy;
+    const uint64_t items = (static_cast<uint64_t>(h->D) >> kTileBits) * gy;
+    const uint64_t ctas = static_cast<uint64_t>(h->n_sm) * c64_ctas_for_stages(S);
+    const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(items, ctas));
+    k_matvec_c64<EPI, ACCUM, S, false, MERGE><<<grid, 32 * (kConsumerWarps + 1), dyn, st>>>(qq, h->d_err);
+  } else {
+    k_matvec_c64<EPI, ACCUM, S, false, MERGE><<<dim3(s.grid, gy), 32 * (kConsumerWarps + 1), dyn, st>>>(q, h->d_err);
+  }
+}
+
 template <typename Real, int EPI, bool ACCUM>
 void launch_pass(const syk_terms* h, const Shape& s, const MV<Real>& q, unsigned gy, cudaStream_t st) {
   if constexpr (std::is_same<Real, float>::value) {
     if (s.R == 8) {
-      constexpr int S = EPI == EPI_STORE ? kStagesC64 : kStagesC64Epi;
-      constexpr size_t dyn = static_cast<size_t>(S) * (1u << kTileBits) * 8u;
-      static std::atomic<uint64_t> configured{0};
-      const uint64_t bit = 1ull << (h->device & 63);
-      if (!(configured.load() & bit)) {
-        SYK_CUDA(cudaFuncSetAttribute(k_matvec_c64<EPI, ACCUM, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(dyn)));
-        configured.fetch_or(bit);
-      }
-      if (EPI == EPI_STORE) {  // one-dimensional over (state, tile) items taken from the handle's counter
-        MV<Real> qq = q;
-        qq.sched = h->d_sched;
-        qq.ny = gy;
-        const uint64_t items = (static_cast<uint64_t>(h->D) >> kTileBits) * gy;
-        const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(items, static_cast<uint64_t>(h->n_sm) * kC64CtasPerSm));
-        k_matvec_c64<EPI, ACCUM, S><<<grid, 32 * (kConsumerWarps + 1), dyn, st>>>(qq, h->d_err);
+      // epilogue passes always take the 3-stage shape (at 72 registers their epilogues spill)
+      if (h->c64_merge()) {
+        launch_c64_pass<EPI, ACCUM, true, kStagesC64Epi>(h, s, q, gy, st);
+      } else if constexpr (EPI != EPI_STORE) {
+        launch_c64_pass<EPI, ACCUM, false, kStagesC64Epi>(h, s, q, gy, st);
       } else {
-        k_matvec_c64<EPI, ACCUM, S><<<dim3(s.grid, gy), 32 * (kConsumerWarps + 1), dyn, st>>>(q, h->d_err);
+        if (h->c64_wide())
+          launch_c64_pass<EPI, ACCUM, false, kStagesC64Epi>(h, s, q, gy, st);
+        else
+          launch_c64_pass<EPI, ACCUM, false, kStagesC64>(h, s, q, gy, st);
       }
       return;
     }
@@ -1015,13 +1032,13 @@ __global__ void k_sum_chunks(const float4* __restrict__ ws, int C, uint64_t n4, 
 // A split complex64 pass: chunks of terms on different CTAs into the
 // workspace, then their sum into q.out (which, for passes after the first,
 // chunk 0 started from).
-template <bool ACCUM>
-void launch_split_pass(const syk_terms* h, int ip, const MV<float>& q, cudaStream_t st) {
-  constexpr size_t dyn = static_cast<size_t>(kStagesC64) * (1u << kTileBits) * 8u;
+template <bool ACCUM, bool MERGE, int S>
+void launch_split_chunks(const syk_terms* h, int ip, const MV<float>& q, cudaStream_t st) {
+  constexpr size_t dyn = static_cast<size_t>(S) * (1u << kTileBits) * 8u;
   static std::atomic<uint64_t> configured{0};
   const uint64_t bit = 1ull << (h->device & 63);
   if (!(configured.load() & bit)) {
-    SYK_CUDA(cudaFuncSetAttribute(k_matvec_c64<EPI_STORE, ACCUM, kStagesC64, true>,
+    SYK_CUDA(cudaFuncSetAttribute(k_matvec_c64<EPI_STORE, ACCUM, S, true, MERGE>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn)));
     configured.fetch_or(bit);
   }
@@ -1033,8 +1050,20 @@ void launch_split_pass(const syk_terms* h, int ip, const MV<float>& q, cudaStrea
   qs.chunk_terms = h->split_terms[ip];
   qs.sched = h->d_sched;
   const uint64_t items = (static_cast<uint64_t>(h->D) >> kTileBits) * C;
-  const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(items, static_cast<uint64_t>(h->n_sm) * kC64CtasPerSm));
-  k_matvec_c64<EPI_STORE, ACCUM, kStagesC64, true><<<grid, 32 * (kConsumerWarps + 1), dyn, st>>>(qs, h->d_err);
+  const uint64_t ctas = static_cast<uint64_t>(h->n_sm) * c64_ctas_for_stages(S);
+  const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(items, ctas));
+  k_matvec_c64<EPI_STORE, ACCUM, S, true, MERGE><<<grid, 32 * (kConsumerWarps + 1), dyn, st>>>(qs, h->d_err);
+}
+
+template <bool ACCUM>
+void launch_split_pass(const syk_terms* h, int ip, const MV<float>& q, cudaStream_t st) {
+  if (h->c64_merge())
+    launch_split_chunks<ACCUM, true, kStagesC64Epi>(h, ip, q, st);
+  else if (h->c64_wide())
+    launch_split_chunks<ACCUM, false, kStagesC64Epi>(h, ip, q, st);
+  else
+    launch_split_chunks<ACCUM, false, kStagesC64>(h, ip, q, st);
+  const int C = h->split_chunks[ip];
   const uint64_t n4 = static_cast<uint64_t>(h->D) / 2;
   const unsigned g2 = static_cast<unsigned>(std::min<uint64_t>((n4 + 255) / 256, static_cast<uint64_t>(h->n_sm) * 8));
   k_sum_chunks<<<g2, 256, 0, st>>>(reinterpret_cast<const float4*>(h->d_split_ws), C, n4,
@@ -1104,7 +1133,7 @@ void plan_split(syk_terms* h) {
   h->split_ws_bytes = 0;
   if (h->dtype != SYK_C64 || h->D < (int64_t(1) << kTileBits)) return;
   const int64_t ntiles = h->D >> kTileBits;
-  const int64_t cap = static_cast<int64_t>(h->n_sm) * kC64CtasPerSm;
+  const int64_t cap = static_cast<int64_t>(h->n_sm) * (h->c64_wide() ? kC64EpiCtasPerSm : kC64CtasPerSm);
   if (2 * ntiles > cap) return;
   int64_t cmax = 1;
   for (size_t p = 0; p < np; ++p) {

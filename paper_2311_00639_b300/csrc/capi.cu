@@ -88,7 +88,9 @@ void upload_table(syk_terms* h) {
     const size_t n = h->terms.size();
     const size_t rb = h->dtype == SYK_C128 ? 8 : 4;
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
-    syk::plan_split(h);
+    std::vector<syk::TermF> rec[2];
+    h->n_runs = syk::build_records(h->terms, h->passes, rec, &h->n_merges);
+    syk::plan_split(h);  // its CTA count depends on whether the records merge terms
     // the passes, then one more: the last pass's tile order with no terms, run
     // for the epilogue after a split last pass
     const size_t pass_bytes = up((h->passes.size() + 1) * sizeof(syk::PassPlan));
@@ -112,8 +114,6 @@ void upload_table(syk_terms* h) {
     char* hr1 = hr0 + rec_bytes;
     uint32_t* hzi = reinterpret_cast<uint32_t*>(hr1 + rec_bytes);
     for (size_t i = 0; i < n; ++i) hzi[i] = h->terms[i].z | (h->terms[i].imag ? 0x80000000u : 0u);
-    std::vector<syk::TermF> rec[2];
-    h->n_runs = syk::build_records(h->terms, h->passes, rec);
     std::memcpy(hr0, rec[0].data(), (n + 1) * sizeof(syk::TermF));
     std::memcpy(hr1, rec[1].data(), (n + 1) * sizeof(syk::TermF));
     for (size_t i = 0; i < n; ++i) {
@@ -233,6 +233,7 @@ int syk_terms_get_info(const syk_terms_t* h, syk_terms_info* info) {
     SYK_CUDA(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     info->device_error = e;
     info->n_tile_reads = h->dtype == SYK_C64 ? h->n_runs : static_cast<int64_t>(h->terms.size());
+    info->n_merged = h->dtype == SYK_C64 ? h->n_merges : 0;
   });
 }
 

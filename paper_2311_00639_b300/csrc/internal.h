@@ -84,6 +84,12 @@ constexpr uint32_t kTermStraggler = 1u;  // the run's input tiles come from HBM 
 constexpr uint32_t kTermRunStart = 2u;   // first term of a run: a new input tile
 constexpr uint32_t kTermRunEnd = 4u;     // last term of a run: its stage is released after it
 constexpr uint32_t kTermImag = 8u;       // coefficient i * c
+// The next record of the pass has the same flip mask x and the same class
+// (imag, z & 1), so the same consumer body on the same staged inputs: the
+// consumer adds this term's signed row coefficients to a running sum and
+// applies the body once, with the sum, at the last term of such a group
+// (dense SYK: many strings share x; x and class equal implies the same run).
+constexpr uint32_t kTermMerge = 16u;
 // Bits 8-13 of flags: the consumer body of the term, 32 imag + 16 (x & 1) +
 // 8 (z & 1) + ((x >> 6) & 7) (class and row permutation of the 8-row layout).
 // Bit 31 of flags, x and z (x and z use at most 31 bits) hold z's bits 6, 7
@@ -100,7 +106,7 @@ void plan_split(syk_terms* h);
 // Complex64 records of both blocks in the kernel's order, n + 1 per block (the
 // last one zero); returns the number of runs (records.cpp).
 int64_t build_records(const std::vector<BlockString>& terms, const std::vector<PassPlan>& passes,
-                      std::vector<TermF> rec[2]);
+                      std::vector<TermF> rec[2], int64_t* n_merges = nullptr);
 // The last pass's tile order with no terms (the epilogue after a split pass).
 PassPlan tail_pass(const PassPlan& last);
 // Reorders `terms` by pass and returns the passes.
@@ -160,6 +166,17 @@ struct syk_terms {
   unsigned long long* d_sched = nullptr;  // complex64 matvec tile counter pair (zero between launches)
   uint32_t* d_zi = nullptr;  // z | (imag << 31) per term (batched engine)
   int64_t n_runs = 0;  // complex64 record runs (input tiles staged per output tile, all passes)
+  int64_t n_merges = 0;  // complex64 records flagged kTermMerge
+  // The merging complex64 kernels (their running sums cost registers and the
+  // 2 x 5 shape) pay when at least half of the terms merge into groups (dense
+  // SYK: 84 %); sparse Hamiltonians merge a term or two and keep the others.
+  bool c64_merge() const { return 2 * n_merges >= static_cast<int64_t>(terms.size()) && n_merges > 0; }
+  // Store passes run 2 stages x 5 CTAs per SM when runs are short (sparse SYK
+  // at N=64: 1.9 terms per staged tile, the spin chain at L=31: 5.6; more
+  // consumer warps hide more latency) and 3 x 4 when runs are long (16 or
+  // more terms per staged tile) or terms merge (dense SYK: each warp's own
+  // load-level parallelism, with 96 registers, matters more).
+  bool c64_wide() const { return c64_merge() || static_cast<int64_t>(terms.size()) >= 16 * std::max<int64_t>(n_runs, 1); }
   // complex64 passes of a small block with many terms are split into chunks of
   // terms applied by different CTAs (plan_split): chunks per pass (1 = not
   // split) and terms per chunk; partial sums go to d_split_ws.

@@ -30,10 +30,11 @@ void plan_view(std::vector<BlockString>&& terms, int L, int dtype, size_t l2_bud
   h.n_sm = n_sm;
   h.terms = std::move(terms);
   h.passes = plan_passes(h.terms, h.L, elem_bytes(dtype), l2_budget_bytes, straggler_ratio);
-  plan_split(&h);
   std::vector<TermF> rec[2];
   const size_t n = h.terms.size();
-  out->n_runs = build_records(h.terms, h.passes, rec);
+  out->n_runs = build_records(h.terms, h.passes, rec, &h.n_merges);
+  out->n_merges = h.n_merges;
+  plan_split(&h);
   out->n_terms = static_cast<int64_t>(n);
   out->n_passes = static_cast<int64_t>(h.passes.size());
   if (out->term_capacity < out->n_terms || out->pass_capacity < out->n_passes) return;

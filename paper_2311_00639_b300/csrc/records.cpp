@@ -11,7 +11,7 @@
 namespace syk {
 
 int64_t build_records(const std::vector<BlockString>& terms, const std::vector<PassPlan>& passes,
-                      std::vector<TermF> rec[2]) {
+                      std::vector<TermF> rec[2], int64_t* n_merges) {
   const size_t n = terms.size();
   // Within each pass, the terms that read the same input tile (equal
   // x >> kTileBits) are made adjacent and flagged as a run.
@@ -27,23 +27,29 @@ int64_t build_records(const std::vector<BlockString>& terms, const std::vector<P
   std::vector<char> pass_end(n + 1, 0);
   for (const auto& ps : passes) pass_end[ps.t1] = 1;
   for (int b = 0; b < 2; ++b) rec[b].assign(n + 1, TermF{0, 0, 0.0f, 0});  // + one zero record: prefetch past the end
-  int64_t n_runs = 0;
+  int64_t n_runs = 0, merges = 0;
   for (size_t k = 0; k < n; ++k) {
     const auto& t = terms[rec_order[k]];
     const uint32_t hi = t.x >> kTileBits;
     const bool start = k == 0 || pass_end[k] || (terms[rec_order[k - 1]].x >> kTileBits) != hi;
     const bool end = k + 1 == n || pass_end[k + 1] || (terms[rec_order[k + 1]].x >> kTileBits) != hi;
+    // same x and class as the next record of the pass (adjacent under rec_key)
+    const bool merge = !(k + 1 == n || pass_end[k + 1]) && terms[rec_order[k + 1]].x == t.x &&
+                       terms[rec_order[k + 1]].imag == t.imag && ((terms[rec_order[k + 1]].z ^ t.z) & 1u) == 0;
     n_runs += start ? 1 : 0;
+    merges += merge ? 1 : 0;
     for (int b = 0; b < 2; ++b) {
       TermF& r = rec[b][k];
       r.x = t.x | (((t.z >> 7) & 1u) << 31);  // z bit 7 (row sign pattern, see TermF)
       r.z = t.z | (((t.z >> 8) & 1u) << 31);  // z bit 8
       r.c = static_cast<float>(t.coef[b]);
       r.flags = (t.straggler ? kTermStraggler : 0u) | (start ? kTermRunStart : 0u) | (end ? kTermRunEnd : 0u) |
+                (merge ? kTermMerge : 0u) |
                 (t.imag ? kTermImag : 0u) | (term_body(t.x, t.z, t.imag) << kTermBodyShift) |
                 (((t.z >> 6) & 1u) << 31);
     }
   }
+  if (n_merges) *n_merges = merges;
   return n_runs;
 }
 

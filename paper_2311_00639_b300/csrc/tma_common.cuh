@@ -128,6 +128,9 @@ constexpr int kC64CtasPerSm = (227 / (16 * kStagesC64 + 2)) < SYK_C64_MAX_CTAS ?
 // thread (at 72 their epilogues spill).
 constexpr int kStagesC64Epi = 3;
 constexpr int kC64EpiCtasPerSm = 4;
+// The stage count of a complex64 matvec kernel fixes its shape: 2 stages run
+// 5 CTAs per SM (72 registers a thread), 3 stages 4 CTAs (96 registers).
+constexpr int c64_ctas_for_stages(int S) { return S == kStagesC64 ? kC64CtasPerSm : kC64EpiCtasPerSm; }
 
 template <bool IMAG, bool XS, bool ZS, int XR>
 __device__ __forceinline__ void c64_rows(const float4* __restrict__ t4, uint32_t pa2, const float (&c)[kRows],
@@ -174,7 +177,13 @@ struct StageRing {
 // (the record array has one spare entry past the last term) so that its
 // latency overlaps the current term.  The term's body index (flags bits
 // 8-13: class imag, x & 1, z & 1 and row permutation x bits 6-8) selects one
-// of 64 compile-time bodies.
+// of 64 compile-time bodies.  Consecutive terms with the same x and class (a
+// merge group, kTermMerge) read the same staged inputs through the same body:
+// their signed row coefficients are summed and the body runs once, at the
+// group's last term (8 adds per merged term instead of 8 loads and 32 FMAs).
+// MERGE = false ignores the flag and applies every term on its own (the same
+// sum, in another rounding order): the kernels of Hamiltonians whose records
+// merge nothing, where the running sums would only cost registers.
 #define SYK_C64_BODY(k)                                                                                          \
   case k:                                                                                                        \
     c64_rows<((k) >> 5) & 1, ((k) >> 4) & 1, ((k) >> 3) & 1, ((k) & 7) % kRows>(t4, pa2, c, a);                 \
@@ -184,20 +193,25 @@ struct StageRing {
   SYK_C64_BODY(k + 5) SYK_C64_BODY(k + 6) SYK_C64_BODY(k + 7)
 // FORCE: [tb0, tb1) is a chunk of a pass whose ends need not be run ends; the
 // chunk's first term starts a run and its last ends one.
-template <int S, bool FORCE = false>
+template <int S, bool FORCE = false, bool MERGE = false>
 __device__ __forceinline__ void c64_terms(int tb0, int tb1, uint4& d, StageRing<S>& ring, float (&a)[kRows][4],
                                           const TermF* __restrict__ rec, uint32_t mt, uint32_t pair_part,
                                           const unsigned char* smem, uint64_t* full_bar, uint64_t* empty_bar,
                                           volatile int* s_err, uint32_t lane) {
   static_assert(kRows == 8, "the row permutation switch covers x bits 6-8");
   bool ok = false;
+  bool pending = false;  // dsum holds the coefficients of earlier terms of a merge group
+  float dsum[kRows] = {};
   const float4* t4 = reinterpret_cast<const float4*>(smem);
   for (int tt = tb0; tt < tb1; ++tt) {
     const uint4 cur = d;
     d = __ldg(reinterpret_cast<const uint4*>(rec + tt + 1));
     const uint32_t x = cur.x, z = cur.y, cb = cur.z;
     uint32_t fl = cur.w;
-    if (FORCE) fl |= (tt == tb0 ? kTermRunStart : 0u) | (tt == tb1 - 1 ? kTermRunEnd : 0u);
+    if (FORCE) {
+      fl |= (tt == tb0 ? kTermRunStart : 0u) | (tt == tb1 - 1 ? kTermRunEnd : 0u);
+      if (tt == tb1 - 1) fl &= ~kTermMerge;  // a chunk's last term closes its group
+    }
     if (fl & kTermRunStart) {
       ok = mbar_wait_bounded(smem_u32(&full_bar[ring.stg]), ring.ph, s_err);
       t4 = reinterpret_cast<const float4*>(smem + ring.stg * (1u << kTileBits) * 8u);
@@ -221,17 +235,33 @@ __device__ __forceinline__ void c64_terms(int tb0, int tb1, uint4& d, StageRing<
         c[6] = __uint_as_float(c2 ^ (z & M));
         c[7] = __uint_as_float(c3 ^ (z & M));
       }
-      const uint32_t pa2 = (pair_part ^ (x & kPairXMask)) >> 1;  // float4 index of the row-0 input pair
-      switch ((fl >> kTermBodyShift) & 63u) {
-        SYK_C64_BODY8(0)
-        SYK_C64_BODY8(8)
-        SYK_C64_BODY8(16)
-        SYK_C64_BODY8(24)
-        SYK_C64_BODY8(32)
-        SYK_C64_BODY8(40)
-        SYK_C64_BODY8(48)
-        SYK_C64_BODY8(56)
-        default: break;
+      if (MERGE && (fl & kTermMerge)) {  // same x and class as the next term: sum the coefficients, apply later
+        if (pending) {
+#pragma unroll
+          for (int r = 0; r < kRows; ++r) dsum[r] += c[r];
+        } else {
+#pragma unroll
+          for (int r = 0; r < kRows; ++r) dsum[r] = c[r];
+          pending = true;
+        }
+      } else {
+        if (MERGE && pending) {  // the group's last term: one body for the whole group
+#pragma unroll
+          for (int r = 0; r < kRows; ++r) c[r] += dsum[r];
+          pending = false;
+        }
+        const uint32_t pa2 = (pair_part ^ (x & kPairXMask)) >> 1;  // float4 index of the row-0 input pair
+        switch ((fl >> kTermBodyShift) & 63u) {
+          SYK_C64_BODY8(0)
+          SYK_C64_BODY8(8)
+          SYK_C64_BODY8(16)
+          SYK_C64_BODY8(24)
+          SYK_C64_BODY8(32)
+          SYK_C64_BODY8(40)
+          SYK_C64_BODY8(48)
+          SYK_C64_BODY8(56)
+          default: break;
+        }
       }
     }
     if (fl & kTermRunEnd) {

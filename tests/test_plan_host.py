@@ -153,8 +153,8 @@ def test_records_runs_flags_and_sign_bits(pkg, N, k, dtype, budget, ratio):
         imag = (fl >> 3) & 1
         body = (fl >> 8) & 63
         assert np.array_equal(body, 32 * imag + 16 * (x & 1) + 8 * (z & 1) + ((x >> 6) & 7))
-        assert np.all(fl & np.uint32(0x7FFFC0F0) == 0)  # no stray bits
-        n_runs_blk = 0
+        assert np.all(fl & np.uint32(0x7FFFC0E0) == 0)  # no stray bits
+        n_runs_blk = n_merges_blk = 0
         for p in plan["passes"]:
             sl = slice(p["t0"], p["t1"])
             # same terms as the plan's pass, as a multiset
@@ -176,7 +176,13 @@ def test_records_runs_flags_and_sign_bits(pkg, N, k, dtype, budget, ratio):
             assert np.array_equal((fl[sl] >> 2) & 1, end.astype(np.uint32))
             n_runs_blk += int(start.sum())
             assert int(start.sum()) == len(np.unique(hi))
+            # merge flag: the next record of the pass has the same x and class
+            cl = term_class(x[sl], z[sl], imag[sl])
+            merge = np.r_[(x[sl][1:] == x[sl][:-1]) & (cl[1:] == cl[:-1]), False]
+            assert np.array_equal((fl[sl] >> 4) & 1, merge.astype(np.uint32))
+            n_merges_blk += int(merge.sum())
         n_runs = n_runs_blk
+        assert plan["n_merges"] == n_merges_blk
     assert plan["n_runs"] == n_runs
 
 
@@ -211,7 +217,11 @@ def test_split_plan_covers_terms(pkg):
         plan = pkg.plan_host(N, q, J, dtype, "jw", 0, 0.0, n_sm)
         D = 1 << (N // 2 - 1)
         ntiles = D >> TILE_BITS
-        cap = n_sm * 5  # resident CTAs of the store passes: 5 per SM
+        # resident CTAs of the store passes: 4 per SM when the handle's runs are long (16 or more
+        # terms per staged tile) or half of its terms merge, else 5
+        n_terms = len(plan["x"])
+        wide = 2 * plan["n_merges"] >= n_terms > 0 and plan["n_merges"] > 0 or n_terms >= 16 * max(plan["n_runs"], 1)
+        cap = n_sm * (4 if wide else 5)
         any_split = False
         for p in plan["passes"]:
             Tp, C, Tc = p["t1"] - p["t0"], p["split_chunks"], p["split_terms"]
@@ -220,7 +230,7 @@ def test_split_plan_covers_terms(pkg):
                 continue
             any_split = True
             assert C >= 2 and Tc >= 32 and (C - 1) * Tc < Tp <= C * Tc  # every chunk non-empty
-            assert C <= -(-cap // ntiles)
+            assert C == -(-Tp // -(-Tp // min(-(-cap // ntiles), Tp // 32)))  # plan_split's chunk count
         assert any_split == (dtype == "c64" and 2 * ntiles <= cap and any(
             p["t1"] - p["t0"] >= 64 for p in plan["passes"]))
 
@@ -331,3 +341,38 @@ def test_plan_strings_rejects_bad_arguments(pkg):
         pkg.plan_strings_host(0, comp)
     comp["x"][0] = 1
     assert len(pkg.plan_strings_host(5, comp)["x"]) == 1
+
+
+def test_merge_groups_of_dense_records_reproduce_oracle_block(pkg):
+    """Dense SYK (every quadruple): many strings share a flip mask. Records
+    flagged "merge" (bit 4) form groups of equal x and class, which the
+    complex64 kernel applies once with the summed signed coefficients. Summing
+    each group's coefficients first and applying one permutation per group
+    reproduces the oracle's block."""
+    N = 16
+    q, J, _ = si.sample_dense_syk(N, seed=2)
+    plan = pkg.plan_host(N, q, J, "c64", "jw", 0, 0.0, 148)
+    n = len(plan["x"])
+    assert plan["n_merges"] > n // 2  # most terms merge at this size
+    D = 1 << (N // 2 - 1)
+    rng = np.random.default_rng(3)
+    psi = rng.normal(size=D) + 1j * rng.normal(size=D)
+    m = np.arange(D, dtype=np.int64)
+    for blk in (0, 1):
+        x, z, c, fl = unpack(plan["records"][blk, :n])
+        out = np.zeros(D, dtype=np.complex128)
+        acc = np.zeros(D)
+        groups = 0
+        for k in range(n):
+            sign = 1.0 - 2.0 * (np.bitwise_count(m & int(z[k])) & 1)
+            acc = acc + c[k] * sign
+            if (fl[k] >> 4) & 1:
+                assert x[k + 1] == x[k] and ((fl[k + 1] >> 3) & 1) == ((fl[k] >> 3) & 1)
+                continue
+            out += (1j if (fl[k] >> 3) & 1 else 1.0) * acc * psi[m ^ int(x[k])]
+            acc = np.zeros(D)
+            groups += 1
+        assert groups == n - plan["n_merges"]
+        ref = ham.csr_block(N, q, J, "jw", blk) @ psi
+        bound = 2.0 ** -24 * np.abs(c).sum() * np.abs(psi).max() * 1.01 + 1e-12
+        assert np.max(np.abs(out - ref)) <= bound
