@@ -242,6 +242,7 @@ def test_dense_syk_split_passes_N24(syk):
     N = 24
     q, J, _ = si.sample_dense_syk(N, 0)
     with syk.Terms(N, q, J, dtype="c64") as h, syk.Terms(N, q, J, dtype="c128") as h2:
+        assert 2 * h.info["n_merged"] >= h.n_terms  # the merging kernels run
         D = h.D
         psi = h.random_state(seed=5, state_id=0, blocks=(0,))[0]
         out = h.apply_H(psi, 0).cpu().numpy()
@@ -254,6 +255,34 @@ def test_dense_syk_split_passes_N24(syk):
         assert st.matvecs > 0
         assert (t.max(t.abs(y64.to(t.complex128) - y128)) / t.max(t.abs(y128))).item() < 2e-5
         assert h.device_error() == 0
+
+
+@pytest.mark.parametrize("N,k", [(30, "dense"), (32, "dense"), (30, 8.0)])
+def test_long_runs_and_merge_groups_vs_complex128(syk, N, k):
+    """Blocks of several tiles whose complex64 passes take the 3-stage kernel
+    shape: dense SYK (N=30: 8 tiles, N=32: 16), where the kernels sum the
+    coefficients of each merge group (equal flip mask and class) and apply one
+    body per group, and sparse k=8 at N=30 (long runs of one staged tile,
+    nothing merged).  The complex128 kernel applies every term on its own.
+    Both blocks, every entry, against the complex128 result, and the
+    complex128 result against sampled rows of the definition."""
+    t = torch()
+    q, J, _ = si.sample_dense_syk(N, 0) if k == "dense" else si.sample_sparse_syk(N, k, r=3)
+    with syk.Terms(N, q, J, dtype="c64") as h, syk.Terms(N, q, J, dtype="c128") as h2:
+        if k == "dense":
+            assert 2 * h.info["n_merged"] >= h.n_terms
+        else:
+            assert 2 * h.info["n_merged"] < h.n_terms and h.n_terms >= 16 * h.info["n_tile_reads"]
+        D = h.D
+        for blk in (0, 1):
+            psi = h.random_state(seed=9, state_id=blk, blocks=(blk,))[0]
+            got = h.apply_H(psi, blk).cpu().numpy()
+            ref = h2.apply_H(psi.to(t.complex128), blk).cpu().numpy()
+            assert rel_err(got, ref) < 2e-5
+            rows = np.arange(0, D, 97, dtype=np.uint64)[:120]
+            at = lambda b, m, blk=blk: si.philox_state(N, 9, blk, np.uint64(b * D) + m)
+            assert rel_err(ref[rows.astype(np.int64)], ham.rows_of_Hpsi(N, q, J, "jw", blk, rows, at)) < 1e-12
+        assert h.device_error() == 0 and h2.device_error() == 0
 
 
 # ------------------------------------------------------------ random state --
