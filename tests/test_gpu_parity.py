@@ -275,9 +275,9 @@ def test_long_runs_and_merge_groups_vs_complex128(syk, N, k):
             assert 2 * h.info["n_merged"] < h.n_terms and h.n_terms >= 16 * h.info["n_tile_reads"]
         D = h.D
         for blk in (0, 1):
-            psi = h.random_state(seed=9, state_id=blk, blocks=(blk,))[0]
-            got = h.apply_H(psi, blk).cpu().numpy()
-            ref = h2.apply_H(psi.to(t.complex128), blk).cpu().numpy()
+            psi = h2.random_state(seed=9, state_id=blk, blocks=(blk,))[0]  # complex128 Philox state
+            got = h.apply_H(psi.to(t.complex64), blk).cpu().numpy()
+            ref = h2.apply_H(psi, blk).cpu().numpy()
             assert rel_err(got, ref) < 2e-5
             rows = np.arange(0, D, 97, dtype=np.uint64)[:120]
             at = lambda b, m, blk=blk: si.philox_state(N, 9, blk, np.uint64(b * D) + m)
