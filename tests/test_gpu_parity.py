@@ -275,7 +275,7 @@ def test_long_runs_and_merge_groups_vs_complex128(syk, N, k):
             assert 2 * h.info["n_merged"] < h.n_terms and h.n_terms >= 16 * h.info["n_tile_reads"]
         D = h.D
         for blk in (0, 1):
-            psi = h2.random_state(seed=9, state_id=blk, blocks=(blk,))[0]  # complex128 Philox state
+            psi = h2.random_state(seed=9, state_id=blk, blocks=(blk,))[blk]  # complex128 Philox state
             got = h.apply_H(psi.to(t.complex64), blk).cpu().numpy()
             ref = h2.apply_H(psi, blk).cpu().numpy()
             assert rel_err(got, ref) < 2e-5
