@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--rows-N", default="30,38,46", help="paper-rows: the N values (k=3, beta=0.05)")
     ap.add_argument("--rows-dense-N", default="30", help="paper-rows: N values of dense SYK rows ('' for none)")
     ap.add_argument("--N", type=int, default=64)
+    ap.add_argument("--dense", action="store_true", help="H psi step on dense SYK (every quadruple) at --N")
     ap.add_argument("--k", type=float, default=4.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-relabel", action="store_true",
@@ -99,9 +100,12 @@ def parse():
 def workload_config(args, T):
     rep = ("jw, Majoranas relabelled for locality (syk_relabel_majoranas)" if not getattr(args, "no_relabel", False)
            else "jw")
-    return {"workload": f"sparse SYK H·psi, N={args.N}, k={args.k:g}, one parity block",
-            "N": args.N, "k": args.k, "terms": T, "D": 1 << (args.N // 2 - 1), "rep": rep,
-            "states": 1, "l2": "inputs larger than L2 (16 GiB per vector), no flush"}
+    D = 1 << (args.N // 2 - 1)
+    kind = f"dense SYK H·psi, N={args.N}" if getattr(args, "dense", False) else f"sparse SYK H·psi, N={args.N}, k={args.k:g}"
+    return {"workload": f"{kind}, one parity block",
+            "N": args.N, "k": "dense" if getattr(args, "dense", False) else args.k, "terms": T, "D": D, "rep": rep,
+            "states": 1, "l2": ("inputs larger than L2 (16 GiB per vector), no flush" if D * 8 > (128 << 20)
+                               else "inputs L2-resident (smaller than the 126 MB L2)")}
 
 
 def locality_terms(syk, N, q, J, args):
@@ -822,7 +826,11 @@ def ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     barrier = (lambda: dist.barrier()) if dist else (lambda: None)
 
-    q0, J0 = replica_terms(si, args.N, args.k, rank)
+    if args.dense:  # every quadruple (the relabelling search is for sparse term lists)
+        args.no_relabel = True
+        q0, J0, _ = si.sample_dense_syk(args.N, seed=rank)
+    else:
+        q0, J0 = replica_terms(si, args.N, args.k, rank)
     q, J, relabel_info = locality_terms(syk, args.N, q0, J0, args)
     h = syk.Terms(args.N, q, J, dtype="c64")
     T, D = h.n_terms, h.D

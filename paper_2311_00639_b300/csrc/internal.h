@@ -90,6 +90,11 @@ constexpr uint32_t kTermImag = 8u;       // coefficient i * c
 // applies the body once, with the sum, at the last term of such a group
 // (dense SYK: many strings share x; x and class equal implies the same run).
 constexpr uint32_t kTermMerge = 16u;
+// Bits 16-23 of a merge group's first record: how many records follow it in
+// the group (groups longer than 256 records are split into groups of at most
+// 256), so that the consumer sums the group in one tight loop.
+constexpr int kTermGroupShift = 16;
+constexpr uint32_t kTermGroupMax = 255u;
 // Bits 8-13 of flags: the consumer body of the term, 32 imag + 16 (x & 1) +
 // 8 (z & 1) + ((x >> 6) & 7) (class and row permutation of the 8-row layout).
 // Bit 31 of flags, x and z (x and z use at most 31 bits) hold z's bits 6, 7

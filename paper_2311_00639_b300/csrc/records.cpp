@@ -27,15 +27,35 @@ int64_t build_records(const std::vector<BlockString>& terms, const std::vector<P
   std::vector<char> pass_end(n + 1, 0);
   for (const auto& ps : passes) pass_end[ps.t1] = 1;
   for (int b = 0; b < 2; ++b) rec[b].assign(n + 1, TermF{0, 0, 0.0f, 0});  // + one zero record: prefetch past the end
+  // merge groups: maximal stretches of a pass with equal x and class
+  // (adjacent under rec_key), split into groups of at most kTermGroupMax + 1
+  // records; merge = the next record is in the same group, glen = records
+  // after a group's first one
+  std::vector<char> same_next(n, 0);
+  for (size_t k = 0; k + 1 < n; ++k) {
+    const auto& a = terms[rec_order[k]];
+    const auto& b = terms[rec_order[k + 1]];
+    same_next[k] = !pass_end[k + 1] && a.x == b.x && a.imag == b.imag && ((a.z ^ b.z) & 1u) == 0;
+  }
+  std::vector<uint32_t> glen(n, 0);
+  std::vector<char> merge_next(n, 0);
+  for (size_t k = 0; k < n;) {
+    size_t e = k;
+    while (e + 1 < n && same_next[e]) ++e;  // [k, e] is one stretch
+    for (size_t a = k; a <= e; a += kTermGroupMax + 1) {
+      const size_t b = std::min(e, a + kTermGroupMax);
+      glen[a] = static_cast<uint32_t>(b - a);
+      for (size_t i = a; i < b; ++i) merge_next[i] = 1;
+    }
+    k = e + 1;
+  }
   int64_t n_runs = 0, merges = 0;
   for (size_t k = 0; k < n; ++k) {
     const auto& t = terms[rec_order[k]];
     const uint32_t hi = t.x >> kTileBits;
     const bool start = k == 0 || pass_end[k] || (terms[rec_order[k - 1]].x >> kTileBits) != hi;
     const bool end = k + 1 == n || pass_end[k + 1] || (terms[rec_order[k + 1]].x >> kTileBits) != hi;
-    // same x and class as the next record of the pass (adjacent under rec_key)
-    const bool merge = !(k + 1 == n || pass_end[k + 1]) && terms[rec_order[k + 1]].x == t.x &&
-                       terms[rec_order[k + 1]].imag == t.imag && ((terms[rec_order[k + 1]].z ^ t.z) & 1u) == 0;
+    const bool merge = merge_next[k];
     n_runs += start ? 1 : 0;
     merges += merge ? 1 : 0;
     for (int b = 0; b < 2; ++b) {
@@ -44,7 +64,7 @@ int64_t build_records(const std::vector<BlockString>& terms, const std::vector<P
       r.z = t.z | (((t.z >> 8) & 1u) << 31);  // z bit 8
       r.c = static_cast<float>(t.coef[b]);
       r.flags = (t.straggler ? kTermStraggler : 0u) | (start ? kTermRunStart : 0u) | (end ? kTermRunEnd : 0u) |
-                (merge ? kTermMerge : 0u) |
+                (merge ? kTermMerge : 0u) | (glen[k] << kTermGroupShift) |
                 (t.imag ? kTermImag : 0u) | (term_body(t.x, t.z, t.imag) << kTermBodyShift) |
                 (((t.z >> 6) & 1u) << 31);
     }

@@ -179,8 +179,11 @@ struct StageRing {
 // 8-13: class imag, x & 1, z & 1 and row permutation x bits 6-8) selects one
 // of 64 compile-time bodies.  Consecutive terms with the same x and class (a
 // merge group, kTermMerge) read the same staged inputs through the same body:
-// their signed row coefficients are summed and the body runs once, at the
-// group's last term (8 adds per merged term instead of 8 loads and 32 FMAs).
+// their signed row coefficients are summed and the body runs once (8 adds per
+// merged term instead of 8 loads and 32 FMAs).  A group's first record holds
+// the group's length (flags bits 16-23): the consumer sums the rest of the
+// group in a tight loop; a chunk of a split pass that starts inside a group
+// keeps running sums record by record (dsum) up to the group's last record.
 // MERGE = false ignores the flag and applies every term on its own (the same
 // sum, in another rounding order): the kernels of Hamiltonians whose records
 // merge nothing, where the running sums would only cost registers.
@@ -235,21 +238,53 @@ __device__ __forceinline__ void c64_terms(int tb0, int tb1, uint4& d, StageRing<
         c[6] = __uint_as_float(c2 ^ (z & M));
         c[7] = __uint_as_float(c3 ^ (z & M));
       }
-      if (MERGE && (fl & kTermMerge)) {  // same x and class as the next term: sum the coefficients, apply later
-        if (pending) {
+      bool apply = true;
+      if (MERGE) {
+        const uint32_t glen = (fl >> kTermGroupShift) & kTermGroupMax;
+        if (glen != 0) {
+          // a merge group's first record: sum the coefficients of the rest
+          // of the group (inside this chunk) in one loop, then run the body
+          int n = static_cast<int>(glen);
+          if (FORCE) n = min(n, tb1 - 1 - tt);
+          // records two ahead: d holds record tt + j, e record tt + j + 1
+          // (never past tb1 <= the pass end, which the record array covers)
+          uint4 e = __ldg(reinterpret_cast<const uint4*>(rec + min(tt + 2, tb1)));
+          for (int j = 1; j <= n; ++j) {
+            const uint4 nx = d;
+            d = e;
+            e = __ldg(reinterpret_cast<const uint4*>(rec + min(tt + j + 2, tb1)));
+            const uint32_t t0 = (__popc(nx.y & mt) << 31) ^ nx.z;
+            const uint32_t t1 = t0 ^ (nx.w & M), t2 = t0 ^ (nx.x & M), t3 = t1 ^ (nx.x & M);
+            c[0] += __uint_as_float(t0);
+            c[1] += __uint_as_float(t1);
+            c[2] += __uint_as_float(t2);
+            c[3] += __uint_as_float(t3);
+            c[4] += __uint_as_float(t0 ^ (nx.y & M));
+            c[5] += __uint_as_float(t1 ^ (nx.y & M));
+            c[6] += __uint_as_float(t2 ^ (nx.y & M));
+            c[7] += __uint_as_float(t3 ^ (nx.y & M));
+            fl = (fl & ~kTermRunEnd) | (nx.w & kTermRunEnd);  // the run may end at the group's last record
+          }
+          tt += n;
+          if (FORCE && tt == tb1 - 1) fl |= kTermRunEnd;
+        } else if (fl & kTermMerge) {
+          // inside a group that began before this chunk: running sums
+          if (pending) {
 #pragma unroll
-          for (int r = 0; r < kRows; ++r) dsum[r] += c[r];
-        } else {
+            for (int r = 0; r < kRows; ++r) dsum[r] += c[r];
+          } else {
 #pragma unroll
-          for (int r = 0; r < kRows; ++r) dsum[r] = c[r];
-          pending = true;
-        }
-      } else {
-        if (MERGE && pending) {  // the group's last term: one body for the whole group
+            for (int r = 0; r < kRows; ++r) dsum[r] = c[r];
+            pending = true;
+          }
+          apply = false;
+        } else if (pending) {  // that group's last record
 #pragma unroll
           for (int r = 0; r < kRows; ++r) c[r] += dsum[r];
           pending = false;
         }
+      }
+      if (apply) {
         const uint32_t pa2 = (pair_part ^ (x & kPairXMask)) >> 1;  // float4 index of the row-0 input pair
         switch ((fl >> kTermBodyShift) & 63u) {
           SYK_C64_BODY8(0)

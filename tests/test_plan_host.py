@@ -153,7 +153,7 @@ def test_records_runs_flags_and_sign_bits(pkg, N, k, dtype, budget, ratio):
         imag = (fl >> 3) & 1
         body = (fl >> 8) & 63
         assert np.array_equal(body, 32 * imag + 16 * (x & 1) + 8 * (z & 1) + ((x >> 6) & 7))
-        assert np.all(fl & np.uint32(0x7FFFC0E0) == 0)  # no stray bits
+        assert np.all(fl & np.uint32(0x7F00C0E0) == 0)  # no stray bits
         n_runs_blk = n_merges_blk = 0
         for p in plan["passes"]:
             sl = slice(p["t0"], p["t1"])
@@ -176,10 +176,25 @@ def test_records_runs_flags_and_sign_bits(pkg, N, k, dtype, budget, ratio):
             assert np.array_equal((fl[sl] >> 2) & 1, end.astype(np.uint32))
             n_runs_blk += int(start.sum())
             assert int(start.sum()) == len(np.unique(hi))
-            # merge flag: the next record of the pass has the same x and class
+            # merge groups: stretches of equal x and class, in groups of at most 256 records;
+            # merge flag = the next record is in the same group, bits 16-23 of a group's first
+            # record = the records after it
             cl = term_class(x[sl], z[sl], imag[sl])
-            merge = np.r_[(x[sl][1:] == x[sl][:-1]) & (cl[1:] == cl[:-1]), False]
+            same = np.r_[(x[sl][1:] == x[sl][:-1]) & (cl[1:] == cl[:-1]), False]
+            merge = np.zeros(len(same), bool)
+            glen = np.zeros(len(same), np.uint32)
+            i = 0
+            while i < len(same):
+                e = i
+                while same[e]:
+                    e += 1
+                for a in range(i, e + 1, 256):
+                    b = min(e, a + 255)
+                    glen[a] = b - a
+                    merge[a:b] = True
+                i = e + 1
             assert np.array_equal((fl[sl] >> 4) & 1, merge.astype(np.uint32))
+            assert np.array_equal((fl[sl] >> 16) & 255, glen)
             n_merges_blk += int(merge.sum())
         n_runs = n_runs_blk
         assert plan["n_merges"] == n_merges_blk
