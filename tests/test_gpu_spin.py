@@ -285,3 +285,38 @@ def test_majorana_calls_refuse_a_pauli_handle():
         rc = L.load().syk_apply_pauli(ts._h, 1, 0, C.c_void_p(v.data_ptr()), C.c_void_p(o.data_ptr()), 1,
                                       C.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert rc == L.SYK_EINVAL
+
+
+def _diagonal_strings(L, n, seed):
+    """n distinct Z-only strings (x = 0) avoiding qubit 0 (z & 1 = 0): one
+    class, so one stretch of equal flip mask, longer than a merge group."""
+    rng = np.random.default_rng(seed)
+    z = rng.choice(np.arange(2, 1 << L, 2), size=n, replace=False).astype(np.uint32)
+    return np.zeros(n, np.uint32), z, rng.normal(size=n)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_long_merge_groups_H_and_krylov(dtype):
+    """600 diagonal strings on L = 12 (two 2048-amplitude tiles): one stretch
+    of equal flip mask and class, which the records split into merge groups
+    of 256, 256 and 88 (complex64: summed in the consumer's group loop, over a
+    pass split into chunks).  H psi against the oracle's CSR matrix, and the
+    Krylov propagator of this diagonal H against its closed form
+    e^{-iHt} x = exp(-i t d) x, with d the diagonal."""
+    import paper_2311_00639_b300 as syk
+
+    L, n = 12, 600
+    x, z, h = _diagonal_strings(L, n, 7)
+    H = spin.csr_H(L, x, z, h)
+    psi = _state(1 << L, 3)
+    with syk.PauliTerms(L, x, z, h, dtype=dtype) as t:
+        if dtype == "c64":
+            assert 2 * t.info["n_merged"] >= t.n_terms
+        got = t.apply_H(_dev(psi, dtype), 0).cpu().numpy()
+        assert _rel(got, H @ psi) < TOL_H[dtype]
+        d = H.diagonal()
+        xv = psi / np.linalg.norm(psi)
+        y, st = t.krylov_evolve(_dev(xv, dtype), 0, 0.0, 0.3, **({"tol": 1e-12} if dtype == "c128" else {}))
+        ref = np.exp(-1j * 0.3 * d) * xv
+        assert _rel(y.cpu().numpy(), ref) < (1e-10 if dtype == "c128" else 5e-5)
+        assert st.matvecs > 0 and t.device_error() == 0

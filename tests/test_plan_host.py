@@ -391,3 +391,35 @@ def test_merge_groups_of_dense_records_reproduce_oracle_block(pkg):
         ref = ham.csr_block(N, q, J, "jw", blk) @ psi
         bound = 2.0 ** -24 * np.abs(c).sum() * np.abs(psi).max() * 1.01 + 1e-12
         assert np.max(np.abs(out - ref)) <= bound
+
+
+def test_long_stretches_split_into_merge_groups_of_256(pkg):
+    """600 strings with one flip mask and class: merge groups of 256, 256 and
+    88 records (bits 16-23 of each group's first record: 255, 255, 87); the
+    records alone, summing each group first, reproduce the oracle's block."""
+    from oracle import spin
+
+    L, n = 12, 600
+    rng = np.random.default_rng(7)
+    z = rng.choice(np.arange(2, 1 << L, 2), size=n, replace=False).astype(np.uint32)
+    x, h = np.zeros(n, np.uint32), rng.normal(size=n)
+    comp = pkg.compile_pauli_host(L, x, z, h)
+    plan = pkg.plan_strings_host(L, comp, "c64", 0, 0.0, 148)
+    R = plan["records"][0, :n]
+    fl = R[:, 3]
+    starts = np.nonzero((fl >> 16) & 255)[0]
+    assert ((fl[starts] >> 16) & 255).tolist() == [255, 255, 87]
+    assert starts.tolist() == [0, 256, 512]
+    assert int(((fl >> 4) & 1).sum()) == plan["n_merges"] == n - 3
+    D = 1 << L
+    psi = rng.normal(size=D) + 1j * rng.normal(size=D)
+    m = np.arange(D, dtype=np.int64)
+    out = np.zeros(D, dtype=np.complex128)
+    xr, zr, c, _ = unpack(R)
+    for a, g in zip(starts.tolist(), ((fl[starts] >> 16) & 255).tolist()):
+        acc = np.zeros(D)
+        for k in range(a, a + g + 1):
+            acc += c[k] * (1.0 - 2.0 * (np.bitwise_count(m & int(zr[k])) & 1))
+        out += acc * psi[m ^ int(xr[a])]
+    ref = spin.csr_H(L, x, z, h) @ psi
+    assert np.max(np.abs(out - ref)) <= 2.0 ** -24 * np.abs(c).sum() * np.abs(psi).max() * 1.01 + 1e-12
