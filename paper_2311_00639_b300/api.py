@@ -60,14 +60,7 @@ def probe_staging(buf, reads: int, jobs_per_cta: int = 4096, stream=None) -> flo
     return v.value
 
 
-def relabel_for_locality(N: int, quads, J, iterations: int = 200000, seed: int = 1, tile_bits: int = 11):
-    """A Jordan-Wigner ordering of the Majoranas with fewer distinct flip
-    patterns above the matvec tile (syk_relabel_majoranas).  Returns
-    {"perm", "quads", "J", "patterns_before", "patterns_after"}: physical
-    Majorana i is Jordan-Wigner Majorana perm[i]; quads / J are the same
-    Hamiltonian in the new labels (for Terms(N, quads, J)); perm[N-2] = N-2
-    and perm[N-1] = N-1."""
-    q, j = _host_arrays(quads, J)
+def _relabel_once(N, q, j, iterations, seed, tile_bits):
     perm = np.zeros(N, np.int32)
     qo = np.zeros_like(q)
     jo = np.zeros_like(j)
@@ -75,7 +68,41 @@ def relabel_for_locality(N: int, quads, J, iterations: int = 200000, seed: int =
     L.check(L.load().syk_relabel_majoranas(N, q.shape[0], q.ctypes.data, j.ctypes.data, int(tile_bits),
                                            int(iterations), C.c_uint64(seed), perm.ctypes.data, qo.ctypes.data,
                                            jo.ctypes.data, C.byref(b), C.byref(a)))
-    return {"perm": perm, "quads": qo, "J": jo, "patterns_before": b.value, "patterns_after": a.value}
+    return {"perm": perm, "quads": qo, "J": jo, "patterns_before": b.value, "patterns_after": a.value,
+            "seed": int(seed)}
+
+
+def relabel_for_locality(N: int, quads, J, iterations: int = 200000, seed: int = 1, tile_bits: int = 11,
+                         restarts: int = 1, dtype: str = "c64"):
+    """A Jordan-Wigner ordering of the Majoranas with fewer distinct flip
+    patterns above the matvec tile (syk_relabel_majoranas).  Returns
+    {"perm", "quads", "J", "patterns_before", "patterns_after", "seed"}:
+    physical Majorana i is Jordan-Wigner Majorana perm[i]; quads / J are the
+    same Hamiltonian in the new labels (for Terms(N, quads, J)); perm[N-2] =
+    N-2 and perm[N-1] = N-1.
+
+    restarts > 1 runs the search from seeds seed, seed + 1, ... (in parallel
+    threads; the library call releases the GIL) and keeps the labels whose
+    default pass plan (syk_plan_host) stages the fewest tiles, counting each
+    pass after the first as one more staged tile and each straggler term,
+    read from HBM, as a third of one (the planner's default HBM/L2 cost
+    ratio); the result then also carries "plan_costs" [(seed, cost)]."""
+    q, j = _host_arrays(quads, J)
+    if restarts <= 1:
+        return _relabel_once(N, q, j, iterations, seed, tile_bits)
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max_workers=int(restarts)) as ex:
+        cands = list(ex.map(lambda sd: _relabel_once(N, q, j, iterations, sd, tile_bits),
+                            range(int(seed), int(seed) + int(restarts))))
+
+    def cost(r):
+        p = plan_host(N, r["quads"], r["J"], dtype=dtype)
+        return p["n_runs"] + len(p["passes"]) - 1 + int(np.sum(p["straggler"])) / 3.0
+
+    costs = [(r["seed"], cost(r)) for r in cands]
+    best = min(range(len(cands)), key=lambda i: (costs[i][1], i))
+    return dict(cands[best], plan_costs=costs)
 
 
 def tridiag_exp(alpha, beta, z: complex, tol: float, force_ql: bool = False, timed: bool = False):

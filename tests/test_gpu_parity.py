@@ -156,18 +156,18 @@ def test_apply_H_dense_syk_and_empty(syk):
 def test_apply_H_sampled_rows_large(syk, dtype, N, relabel):
     """N=40 and N=64: sampled rows from the definition against a
     counter-based typical state.  The relabelled N=64 complex64 case is the
-    benchmark's timed H psi in its launch configuration (locality-ordered
-    labels from syk_relabel_majoranas, default 5-pass plan); the oracle
+    benchmark's timed H psi in its launch configuration (the benchmark's
+    locality-ordered labels, default 5-pass plan); the oracle
     evaluates the rows of that relabelled Hamiltonian from its definition."""
     t = torch()
     q, J, _ = si.sample_sparse_syk(N, 4, r=0)
-    if relabel:
-        r = syk.relabel_for_locality(N, q, J)
+    if relabel:  # the benchmark's search: 3 restarts of 3 000 000 moves
+        r = syk.relabel_for_locality(N, q, J, iterations=3_000_000, restarts=3)
         q, J = r["quads"], r["J"]
     rng = np.random.default_rng(5)
     with syk.Terms(N, q, J, dtype=dtype) as h:
         if relabel:
-            assert h.info["n_passes"] == 5 and h.info["n_tile_reads"] == 140
+            assert h.info["n_passes"] == 5 and h.info["n_tile_reads"] == 133
         D = h.D
         psiU, psiD = h.random_state(seed=77, state_id=3)
         for blk, psi in ((0, psiU), (1, psiD)):
