@@ -97,6 +97,7 @@ struct BatchArgs {
   int* err;       // set when a bounded wait expires
   double brk;     // Lanczos breakdown threshold, relative to |alpha_j| + beta_{j-1}
   int* slot_cnt;  // [max slots] blocks of the slot done with k_b_axpy_norm (0 between launches)
+  int* alpha_cnt;  // [max slots] blocks of the slot done with the matvec (0 between launches)
   double* lsc;    // [max slots][2] for the next matvec: s_j = 1 / beta_{j-1}, beta_{j-1} s_{j-1}
   const int* slot_group;  // [max slots] tick group of each live slot (-1: dead)
   int group;              // the group this tick's graph advances
@@ -123,6 +124,27 @@ __device__ __forceinline__ double slot_sum(const double* part, int2 r) { return 
 // s_j = 1 / beta_{j-1} (s_0 = 1) into a scalar it applies anyway.  Only call
 // this for betas written by an earlier launch.
 __device__ __forceinline__ double basis_scale(const KScalars* sc, int j) { return j > 0 ? 1.0 / sc->beta[j - 1] : 1.0; }
+
+// Finish the matvec of Lanczos step j: the last block of the slot to get here
+// (after every block's alpha partial is visible) sums the partials once, in
+// the fixed order of slot_sum, into alpha_j, which k_b_axpy_norm then reads.
+// Thread 0 has written this block's partial.  All threads of the block call it.
+__device__ __forceinline__ void matvec_finish_alpha(const BatchArgs& a, KScalars* sc, int si, int j, int2 rg) {
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();  // the partial is visible before this block counts itself done
+    last = atomicAdd(a.alpha_cnt + si, 1) == rg.y - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    const double al = slot_sum(a.partA, rg);
+    if (threadIdx.x == 0) {
+      sc->alpha[j] = al;
+      a.alpha_cnt[si] = 0;
+    }
+  }
+}
 
 // Finish Lanczos step j (run by the last block of the slot to leave
 // k_b_axpy_norm(j), after every block's norm partial is visible):
@@ -440,6 +462,7 @@ __global__ void __launch_bounds__(kBlk) k_b_matvec(BatchArgs a, int j) {
   }
   part = block_sum(part);
   if (threadIdx.x == 0) a.partA[blockIdx.x] = part * sjd;
+  matvec_finish_alpha(a, sc, si, j, rg);
 }
 
 // complex64 slots with D >= 2048: the TMA-staged pair-layout matvec of the
@@ -455,7 +478,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
   const int2 rg = a.blk_range[si];
   const BSlot& s = a.slots[si];
   if (rg.y <= 0 || !s.live || !s.ev || s.done || s.D < (1u << kTileBits)) return;
-  const KScalars* sc = a.sc + si;
+  KScalars* sc = a.sc + si;
   if (sc->m_eff <= j) return;
   const uint32_t tl = blockIdx.x - rg.x;
 
@@ -543,6 +566,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), kC64CtasPerSm) k_b_
     a.partA[blockIdx.x] = part * (j > 0 ? a.lsc[2 * si] : 1.0);
     if (s_err) atomicExch(a.err, 1);
   }
+  matvec_finish_alpha(a, sc, si, j, rg);
 }
 
 template <typename Real>
@@ -553,8 +577,7 @@ __global__ void __launch_bounds__(kBlk) k_b_axpy_norm(BatchArgs a, int j) {
   const BSlot& s = a.slots[si];
   KScalars* sc = a.sc + si;
   if (sc->m_eff <= j) return;
-  const double al = slot_sum(a.partA, rg);
-  if (tl == 0 && threadIdx.x == 0) sc->alpha[j] = al;
+  const double al = sc->alpha[j];  // summed once by the matvec's last block of the slot
   const Real alr = static_cast<Real>(al * basis_scale(sc, j));  // v_j = s_j basis[j]
   const auto* v = basis<Real>(s, j);
   auto* w = basis<Real>(s, j + 1);
@@ -644,7 +667,7 @@ struct Batch {
   int2* d_blk_range = nullptr;
   double* d_part = nullptr;  // 2 x max blocks
   int* d_err = nullptr;      // bounded-wait failure flag
-  int* d_slot_cnt = nullptr;  // per slot: blocks done with axpy_norm (zero between launches)
+  int* d_slot_cnt = nullptr;  // per slot: blocks done with axpy_norm, then with the matvec (zero between launches)
   double* d_lsc = nullptr;    // per slot: the next matvec's two Lanczos scalars
   size_t max_blocks = 0;  // per tick group: block map and partials of group g at offset g * max_blocks
   // Live slots are split into two tick groups, each with its own graph and
@@ -722,6 +745,7 @@ void capture_tick(Batch& b, int grp) {
   a.err = b.d_err;
   a.brk = sizeof(Real) == 4 ? 1e-7 : 1e-14;
   a.slot_cnt = b.d_slot_cnt;
+  a.alpha_cnt = b.d_slot_cnt + b.max_slots;
   a.lsc = b.d_lsc;
   a.slot_group = b.d_slot_group;
   a.group = grp;
@@ -898,8 +922,8 @@ int syk_batch_create(int dtype, int max_slots, size_t max_bytes, const syk_krylo
     SYK_CUDA(cudaMemset(b.d_blk_range, 0, max_slots * sizeof(int2)));
     SYK_CUDA(cudaMalloc(&b.d_part, 2 * syk::kGroups * b.max_blocks * sizeof(double)));
     SYK_CUDA(cudaMalloc(&b.d_err, sizeof(int)));
-    SYK_CUDA(cudaMalloc(&b.d_slot_cnt, max_slots * sizeof(int)));
-    SYK_CUDA(cudaMemset(b.d_slot_cnt, 0, max_slots * sizeof(int)));
+    SYK_CUDA(cudaMalloc(&b.d_slot_cnt, 2 * max_slots * sizeof(int)));  // axpy_norm, then matvec counters
+    SYK_CUDA(cudaMemset(b.d_slot_cnt, 0, 2 * max_slots * sizeof(int)));
     SYK_CUDA(cudaMalloc(&b.d_lsc, 2 * max_slots * sizeof(double)));
     SYK_CUDA(cudaMemset(b.d_err, 0, sizeof(int)));
     SYK_CUDA(cudaMemset(b.d_slots, 0, max_slots * sizeof(syk::BSlot)));
