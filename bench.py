@@ -114,15 +114,37 @@ def workload_config(args, T):
 RELABEL = {"iterations": 3_000_000, "restarts": 3}
 
 
+_relabel_cache = {}
+
+
+def _relabel(syk, N, q, J, M=None):
+    """relabel_for_locality with the benchmark's search, once per term list."""
+    import numpy as np
+
+    key = (N, np.asarray(q, np.int32).tobytes(), np.asarray(J, np.float64).tobytes(),
+           None if M is None else np.asarray(M, np.float64).tobytes())
+    if key not in _relabel_cache:
+        _relabel_cache[key] = syk.relabel_for_locality(N, q, J, M=M, **RELABEL)
+    return _relabel_cache[key]
+
+
 def locality_terms(syk, N, q, J, args):
     """The benchmark Hamiltonian in the library's locality-ordered
     Jordan-Wigner labels (the same operator up to a unitary change of basis;
     fewer staged input tiles per output tile), unless --no-relabel."""
     if getattr(args, "no_relabel", False):
         return q, J, None
-    r = syk.relabel_for_locality(N, q, J, **RELABEL)
+    r = _relabel(syk, N, q, J)
     return r["quads"], r["J"], {"patterns_before": r["patterns_before"], "patterns_after": r["patterns_after"],
                                 "search": dict(RELABEL, seed=r["seed"], plan_costs=r["plan_costs"])}
+
+
+def locality_terms_complex(syk, N, q, J, M, args):
+    """The same relabelling for couplings J + iM (the library flips M with J)."""
+    if getattr(args, "no_relabel", False):
+        return q, J, M, None
+    r = _relabel(syk, N, q, J, M)
+    return r["quads"], r["J"], r["M"], {"patterns_after": r["patterns_after"], "seed": r["seed"]}
 
 
 # ------------------------------------------------------------------ clocks --
@@ -652,8 +674,9 @@ def outlook_hpsi(args, syk, si, torch):
     try:
         q, J, _ = si.sample_sparse_syk(64, 4.0, r=0)
         M = 0.1 * np.random.default_rng(900).normal(size=len(J)) * math.sqrt(float(np.mean(J ** 2)))
+        q, J, M, relabel = locality_terms_complex(syk, 64, q, J, M, args)
         with syk.Terms.complex(64, q, J, M, dtype="c64") as t:
-            out["nonhermitian_N64"] = hpsi_rate(t, steps, 2, torch, n_input=len(J))
+            out["nonhermitian_N64"] = dict(hpsi_rate(t, steps, 2, torch, n_input=len(J)), relabelled=bool(relabel))
     except Exception as e:  # informational only
         out["nonhermitian_N64"] = {"error": str(e)[:300]}
     return out
@@ -748,8 +771,10 @@ def nonherm_leg(args, syk, si, torch):
         return q, J, M
 
     q, J, M = couplings(args.N, args.k, 0)
+    q, J, M, relabel = locality_terms_complex(syk, args.N, q, J, M, args)
     out = {"workload": f"non-Hermitian sparse SYK N={args.N}, k={args.k:g}, couplings J + iM (M ~ 0.1 J), "
-                       "one parity block"}
+                       "one parity block" + (", Majoranas relabelled for locality" if relabel else ""),
+           "relabel": relabel}
     with syk.Terms.complex(args.N, q, J, M, dtype="c64") as h:
         out["Hpsi_c64"] = dict(hpsi_rate(h, args.steps, args.warmup, torch, n_input=len(J)),
                                note="rate counts input terms (quads); each compiles to two strings")

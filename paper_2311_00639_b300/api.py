@@ -73,7 +73,7 @@ def _relabel_once(N, q, j, iterations, seed, tile_bits):
 
 
 def relabel_for_locality(N: int, quads, J, iterations: int = 200000, seed: int = 1, tile_bits: int = 11,
-                         restarts: int = 1, dtype: str = "c64"):
+                         restarts: int = 1, dtype: str = "c64", M=None):
     """A Jordan-Wigner ordering of the Majoranas with fewer distinct flip
     patterns above the matvec tile (syk_relabel_majoranas).  Returns
     {"perm", "quads", "J", "patterns_before", "patterns_after", "seed"}:
@@ -86,10 +86,25 @@ def relabel_for_locality(N: int, quads, J, iterations: int = 200000, seed: int =
     default pass plan (syk_plan_host) stages the fewest tiles, counting each
     pass after the first as one more staged tile and each straggler term,
     read from HBM, as a third of one (the planner's default HBM/L2 cost
-    ratio); the result then also carries "plan_costs" [(seed, cost)]."""
+    ratio); the result then also carries "plan_costs" [(seed, cost)].
+
+    M (optional): imaginary parts of complex couplings J + iM.  Terms keep
+    their order and each is the original times (-1)^(inversions of its
+    reordered indices), so the result's "M" is M with J's sign flips (the
+    search itself looks at the flip patterns only)."""
     q, j = _host_arrays(quads, J)
     if restarts <= 1:
-        return _relabel_once(N, q, j, iterations, seed, tile_bits)
+        res = _relabel_once(N, q, j, iterations, seed, tile_bits)
+    else:
+        res = _relabel_multistart(N, q, j, iterations, seed, tile_bits, restarts, dtype)
+    if M is not None:  # the sign of each reordered product, from the permutation (J may be 0)
+        v = res["perm"][q]
+        inv = sum((v[:, a] > v[:, b]).astype(np.int64) for a in range(4) for b in range(a + 1, 4))
+        res["M"] = np.asarray(M, dtype=np.float64) * np.where(inv & 1, -1.0, 1.0)
+    return res
+
+
+def _relabel_multistart(N, q, j, iterations, seed, tile_bits, restarts, dtype):
     from concurrent.futures import ThreadPoolExecutor
 
     with ThreadPoolExecutor(max_workers=int(restarts)) as ex:

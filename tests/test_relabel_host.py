@@ -95,3 +95,25 @@ def test_multistart_keeps_the_cheapest_plan_and_the_benchmark_labels():
     plan = syk.plan_host(N, b["quads"], b["J"], dtype="c64")
     assert b["patterns_after"] == 133 and len(plan["passes"]) == 5 and plan["n_runs"] == 133
     assert int(np.sum(plan["straggler"])) == 8
+
+
+def test_relabelled_complex_couplings_keep_the_spectrum():
+    """Couplings J + iM: the relabelled Hamiltonian (quads, J and M with the
+    same sign flips) has the same complex spectrum as the original (dense
+    non-Hermitian oracle, N = 12), for one search and for a multi-start one."""
+    import paper_2311_00639_b300 as syk
+    from oracle import nonherm as nh
+
+    N = 12
+    q, J, _ = si.sample_sparse_syk(N, 4, r=5)
+    M = 0.3 * np.random.default_rng(3).normal(size=len(J))
+    ev0 = np.sort_complex(np.linalg.eigvals(nh.dense_H(N, q, J, M, "jw")))
+    for kw in ({"iterations": 5000, "seed": 2}, {"iterations": 3000, "restarts": 2}):
+        r = syk.relabel_for_locality(N, q, J, M=M, tile_bits=2, **kw)
+        assert not np.array_equal(r["perm"], np.arange(N))  # a real relabelling
+        ev1 = np.sort_complex(np.linalg.eigvals(nh.dense_H(N, r["quads"], r["J"], r["M"], "jw")))
+        assert np.max(np.abs(ev1 - ev0)) < 1e-10
+        # the planted mistake of keeping M's signs while J's flip shows in the spectrum
+        assert np.any(np.sign(r["J"]) != np.sign(J))
+        bad = np.sort_complex(np.linalg.eigvals(nh.dense_H(N, r["quads"], r["J"], M, "jw")))
+        assert np.max(np.abs(bad - ev0)) > 1e-6
